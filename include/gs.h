@@ -1,0 +1,156 @@
+/*
+ * gs.h -- C ABI of the GB300 generalized-sampling library (libgs.so).
+ *
+ * Generalized sampling (Jacobsen, Nielsen, Rasmussen, "Generalized Sampling in
+ * Julia"): from Fourier samples w^s_m = f-hat(xi_m), m = 1..M, estimate the
+ * coefficients of f in the boundary-corrected Daubechies scaling-function basis
+ * V_J^int of [-1/2, 1/2] (Sec. 3.3, eq. modified_Daubechies_span) or of its
+ * tensor square (Sec. 5) by weighted least squares (Sec. 2, eq. least_squares;
+ * Sec. 4.1, eq. weighted_least_squares).  The library applies the change-of-basis
+ * matrix T (Sec. 4, eq. CoB_block_1D; Sec. 5, eq. 2Dwavelet_border_division;
+ * App. C) and its adjoint without forming it, and solves the least-squares
+ * problem with CGLS (Sec. 6.3).
+ *
+ * Conventions (all entry points)
+ *   - Complex values are interleaved (re, im): complex128 = 2 doubles,
+ *     complex64 = 2 floats.
+ *   - Coefficients: 1D vector of N = 2^J values, index i = 0..N-1 is the
+ *     function phi^int_{J, i - N/2} (left edge functions first, Sec. 3.3);
+ *     2D array of N*N values stored x-fastest: X(i, j) at i + N*j, i along x
+ *     (App. C's column-major vec; Sec. 5).
+ *   - Samples: M values in the caller's order of xi.
+ *   - Rows of T carry the density weight sqrt(mu_m) (Sec. 4.1).  Data passed to
+ *     gs_solve must already be weighted: y_m = sqrt(mu_m) * f-hat(xi_m).
+ *   - Device pointers are CUDA device (or managed) memory owned by the caller;
+ *     host pointers are read during the call only.  "stream" is a cudaStream_t
+ *     (NULL = legacy default stream); all device work of a call is ordered on it.
+ *   - No call synchronises the device except gs_plan_* (which return after the
+ *     tables are built) and gs_solve (which reads its stop flag).
+ *   - Errors are returned as gs_status; gs_last_error_detail() gives a
+ *     thread-local description.  Nothing aborts or throws across the ABI.
+ *   - A plan is not thread-safe: do not run two calls on one plan concurrently.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_plan_s* gs_plan;
+
+typedef enum {
+  GS_OK = 0,
+  GS_EINVAL = 1,        /* bad argument (sizes, NULL, non-finite xi or weights) */
+  GS_ENOMEM = 2,        /* device or host allocation failed */
+  GS_ECUDA = 3,         /* a CUDA runtime call failed (detail has the CUDA error) */
+  GS_ENOTCONV = 4,      /* gs_solve hit maxit before the tolerance */
+  GS_EBREAKDOWN = 5,    /* CGLS breakdown: ||T p|| = 0 or a non-finite step */
+  GS_ETIMEOUT = 6,      /* a bounded device wait gave up */
+  GS_EUNSUPPORTED = 7   /* a valid request this build does not implement */
+} gs_status;
+
+/* Arithmetic of one apply. */
+typedef enum {
+  GS_FP64 = 0, /* complex128 in and out, float64 arithmetic, KB half-width kb_m_hi */
+  GS_FP32 = 1  /* complex64 in and out, float32 arithmetic, KB half-width kb_m_lo  */
+} gs_precision;
+
+/* Plan options; pass NULL for the defaults in brackets. */
+typedef struct {
+  int kb_m_hi;  /* Kaiser-Bessel half-width (taps per dim = 2m) for GS_FP64 applies [8] */
+  int kb_m_lo;  /* Kaiser-Bessel half-width for GS_FP32 applies [4] */
+  int sigma;    /* oversampling factor of the NFFT grid, 2 or 4 [2] */
+  int direct;   /* 1: evaluate T entry by entry (O(M N^d) per apply, small problems);
+                   0: NFFT path; -1: choose (direct when M * N^d <= 2^20) [-1] */
+} gs_opts;
+
+/* Build a 1D plan: the representation of T (paper: Freq2Wave(xi, "dbp", J[, bandwidth]),
+ * Sec. 6.1-6.2).  Validation: p in 1..6 (p = 1 is Haar), 2^J >= 2p (Sec. 3.3),
+ * J <= 20, M >= 1, xi finite.
+ *   out        receives the plan (NULL on error)
+ *   xi         host, M sampling frequencies (any order, any range; Sec. 3.1)
+ *   p, J       vanishing moments and scale: N = 2^J coefficients
+ *   bandwidth  > 0: density weights mu = 1D Voronoi cell lengths, outer cells
+ *              closed by [-bandwidth, bandwidth] (Sec. 4.1); <= 0: mu = 1
+ *   weights    host, M density weights mu_m >= 0 (overrides bandwidth), or NULL
+ *   stream     cudaStream_t for the table-building kernels */
+gs_status gs_plan_1d(gs_plan* out, const double* xi, int64_t M, int p, int J,
+                     double bandwidth, const double* weights, const gs_opts* opts,
+                     void* stream);
+
+/* Build a 2D plan (Sec. 5, App. B, App. C).  xi is host, M x 2 interleaved
+ * (xi_x, xi_y); weights is host M or NULL (mu = 1). */
+gs_status gs_plan_2d(gs_plan* out, const double* xi, int64_t M, int p, int J,
+                     const double* weights, const gs_opts* opts, void* stream);
+
+void gs_plan_destroy(gs_plan plan);
+
+/* Sizes of a plan: dims (1 or 2), M, N (per dimension), ncoef (N or N*N). */
+gs_status gs_plan_sizes(gs_plan plan, int* dims, int64_t* M, int64_t* N, int64_t* ncoef);
+
+/* y = T x (Sec. 4, eq. CoB_block_1D; Sec. 5; App. C: interior by NFFT, corners
+ * and sides by the boundary factors).
+ *   x  device, ncoef complex (complex128 for GS_FP64, complex64 for GS_FP32)
+ *   y  device, M complex of the same type; overwritten */
+gs_status gs_apply_T(gs_plan plan, int precision, const void* x, void* y, void* stream);
+
+/* x = T^H y (Sec. 3.2 adjoint NDFT; App. C adjoint).  Buffers as gs_apply_T. */
+gs_status gs_apply_TH(gs_plan plan, int precision, const void* y, void* x, void* stream);
+
+/* Solver settings for gs_solve. */
+typedef enum {
+  GS_SOLVE_FP64 = 0,  /* textbook CGLS with GS_FP64 applies throughout */
+  GS_SOLVE_MIXED = 1  /* iterative refinement: x += d, d from a CG pass on the normal
+                         equations T^H T d = T^H r with GS_FP32 applies and float64
+                         scalars; r = y - T x with a GS_FP64 forward apply between
+                         passes; T^H r (the pass rhs and the stop test) with a GS_FP32
+                         adjoint when tol >= 1e-7, else GS_FP64 */
+} gs_solve_mode;
+
+typedef struct {
+  double tol;     /* stop when ||T^H (y - T x)|| <= tol * ||T^H y|| [1e-6] */
+  int maxit;      /* total CGLS iteration cap [1000] */
+  int mode;       /* gs_solve_mode [GS_SOLVE_MIXED] */
+  int x0_given;   /* 1: x holds a starting guess on entry; 0: start from x = 0 [0] */
+  int max_outer;  /* refinement passes in GS_SOLVE_MIXED [8] */
+  double inner_rtol; /* GS_SOLVE_MIXED: a pass stops when its ||T^H (r - T d)|| falls
+                        by this factor (or below tol ||T^H y|| / 2); 0 = default [1e-4] */
+} gs_solve_opts;
+
+typedef struct {
+  int iterations;     /* CGLS iterations, all passes */
+  int outer;          /* refinement passes (1 in GS_SOLVE_FP64) */
+  double rel_normres; /* ||T^H (y - T x)|| / ||T^H y|| at exit: x and r = y - T x in FP64,
+                         T^H r in the stop-test precision of the mode */
+  double rel_res;     /* ||y - T x|| / ||y|| at exit */
+  int status;         /* gs_status of the solve */
+} gs_solve_info;
+
+/* Weighted least squares x = argmin ||T x - y|| (Sec. 2, eq. least_squares; the
+ * paper's T \ y, Sec. 6.2) by CGLS, stopped on the normal-equation residual.
+ *   y    device, M complex128 (weighted data)
+ *   x    device, ncoef complex128; the solution (and the start if x0_given)
+ *   info host, may be NULL
+ * Returns GS_ENOTCONV when maxit is reached (x holds the last iterate). */
+gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* opts,
+                   gs_solve_info* info, void* stream);
+
+/* Host-only (no CUDA call): the plan-time constants for p vanishing moments, so
+ * they can be checked without a GPU.  h: 2p filter taps h_k, k = -p+1..p, with
+ * sum 1 (App. A).  For p >= 2 also the edge matrices of App. A.1, row-major:
+ * U_left, U_right (p x p, = H / sqrt2), V_left, V_right (p x (2p-1), = h / sqrt2,
+ * columns m = p..3p-2) and v1(0) for both sides (p each).  Any of the output
+ * pointers may be NULL.  GS_EINVAL for p outside 1..6. */
+gs_status gs_boundary_constants(int p, double* h, double* U_left, double* V_left, double* v0_left,
+                                double* U_right, double* V_right, double* v0_right);
+
+const char* gs_strerror(gs_status s);
+const char* gs_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -1,0 +1,264 @@
+// extern "C" entry points of libgs (declared in include/gs.h): validation,
+// plan lifetime, applies in the caller's sample order, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+static thread_local char g_detail[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+  va_end(ap);
+}
+
+gs_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return GS_ECUDA;
+}
+
+static void free_prec_f(PrecData<float>& D) {
+  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
+                D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+static void free_prec_d(PrecData<double>& D) {
+  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
+                D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+static void free_plan(Plan* P) {
+  void* ps[] = {P->perm, P->fl, P->xi_sorted, P->bin_start, P->work, P->work_start,
+                P->red, P->scal, P->flag, P->y64, P->r64, P->x64};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  free_prec_d(P->d);
+  free_prec_f(P->f);
+}
+
+static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, int p, int J,
+                           double bandwidth, const double* weights, const gs_opts* opts, void* stream) {
+  if (!out) {
+    set_error("out is NULL");
+    return GS_EINVAL;
+  }
+  *out = nullptr;
+  if (!xi || M < 1 || M > ((int64_t)1 << 31) - 1) {
+    set_error("need xi != NULL and 1 <= M < 2^31 (M = %lld)", (long long)M);
+    return GS_EINVAL;
+  }
+  if (p < 1 || p > GS_MAX_P) {
+    set_error("p = %d outside 1..%d", p, GS_MAX_P);
+    return GS_EINVAL;
+  }
+  if (J < 1 || J > 20 || (dims == 2 && J > 13) || (1LL << J) < 2LL * p) {
+    set_error("J = %d invalid for p = %d (need 2^J >= 2p, J <= 20 in 1D, <= 13 in 2D)", J, p);
+    return GS_EINVAL;
+  }
+  for (int64_t i = 0; i < M * dims; ++i)
+    if (!std::isfinite(xi[i])) {
+      set_error("xi[%lld] is not finite", (long long)i);
+      return GS_EINVAL;
+    }
+  if (weights)
+    for (int64_t i = 0; i < M; ++i)
+      if (!std::isfinite(weights[i]) || weights[i] < 0.0) {
+        set_error("weights[%lld] is negative or not finite", (long long)i);
+        return GS_EINVAL;
+      }
+  gs_opts o = {8, 4, 2, -1};
+  if (opts) o = *opts;
+  if (o.kb_m_hi < 2 || o.kb_m_hi > 12 || o.kb_m_lo < 2 || o.kb_m_lo > 12 || (o.sigma != 2 && o.sigma != 4)) {
+    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..12), sigma = %d (2 or 4)", o.kb_m_hi, o.kb_m_lo,
+              o.sigma);
+    return GS_EINVAL;
+  }
+  gs_plan_s* h = new (std::nothrow) gs_plan_s();
+  if (!h) {
+    set_error("host allocation failed");
+    return GS_ENOMEM;
+  }
+  Plan* P = &h->P;
+  P->dims = dims;
+  P->p = p;
+  P->J = J;
+  P->b = (p == 1) ? 0 : p;
+  P->M = M;
+  P->N = (int64_t)1 << J;
+  P->ncoef = (dims == 1) ? P->N : P->N * P->N;
+  P->sigma = o.sigma;
+  P->n = P->N * o.sigma;
+  P->m_hi = o.kb_m_hi;
+  P->m_lo = o.kb_m_lo;
+  P->bandwidth = bandwidth;
+  int mmax = o.kb_m_hi > o.kb_m_lo ? o.kb_m_hi : o.kb_m_lo;
+  const int tile = (dims == 1) ? TILE1 : TILE2;
+  const int64_t eff_tile = P->n < tile ? P->n : tile;
+  bool nfft_ok = (eff_tile >= mmax) && (P->n >= 2 * mmax);
+  if (dims == 1 && P->n > 8192) nfft_ok = false;  // one-CTA FFT in float64
+  if (dims == 2 && P->n > 1024) nfft_ok = false;  // float64 column-pass tiles in shared memory
+  if (o.direct == 1) P->direct = 1;
+  else if (o.direct == 0) {
+    if (!nfft_ok) {
+      set_error("NFFT path needs n = sigma 2^J >= 2 m, a tile >= m and n <= %d", dims == 1 ? 8192 : 1024);
+      delete h;
+      return GS_EUNSUPPORTED;
+    }
+    P->direct = 0;
+  } else {
+    P->direct = (!nfft_ok || (double)M * (double)P->ncoef <= 1048576.0) ? 1 : 0;
+  }
+  if (!build_constants(p, &P->k)) {
+    set_error("boundary construction failed for p = %d", p);
+    delete h;
+    return GS_EUNSUPPORTED;
+  }
+  GS_CUDA(cudaGetDevice(&P->dev));
+  gs_status s = build_plan(P, xi, weights, (cudaStream_t)stream);
+  if (s != GS_OK) {
+    free_plan(P);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+gs_status gs_plan_1d(gs_plan* out, const double* xi, int64_t M, int p, int J, double bandwidth,
+                     const double* weights, const gs_opts* opts, void* stream) {
+  return make_plan(out, 1, xi, M, p, J, bandwidth, weights, opts, stream);
+}
+
+gs_status gs_plan_2d(gs_plan* out, const double* xi, int64_t M, int p, int J, const double* weights,
+                     const gs_opts* opts, void* stream) {
+  return make_plan(out, 2, xi, M, p, J, 0.0, weights, opts, stream);
+}
+
+void gs_plan_destroy(gs_plan plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  free_plan(&plan->P);
+  delete plan;
+}
+
+gs_status gs_plan_sizes(gs_plan plan, int* dims, int64_t* M, int64_t* N, int64_t* ncoef) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return GS_EINVAL;
+  }
+  if (dims) *dims = plan->P.dims;
+  if (M) *M = plan->P.M;
+  if (N) *N = plan->P.N;
+  if (ncoef) *ncoef = plan->P.ncoef;
+  return GS_OK;
+}
+
+gs_status gs_apply_T(gs_plan plan, int precision, const void* x, void* y, void* stream) {
+  if (!plan || !x || !y) {
+    set_error("plan, x and y must be non-NULL");
+    return GS_EINVAL;
+  }
+  Plan* P = &plan->P;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GS_FP64)
+    return apply_T<double>(P, P->d, (const double2*)x, (double2*)y, P->perm, st);
+  if (precision == GS_FP32)
+    return apply_T<float>(P, P->f, (const float2*)x, (float2*)y, P->perm, st);
+  set_error("unknown precision %d", precision);
+  return GS_EINVAL;
+}
+
+gs_status gs_apply_TH(gs_plan plan, int precision, const void* y, void* x, void* stream) {
+  if (!plan || !x || !y) {
+    set_error("plan, x and y must be non-NULL");
+    return GS_EINVAL;
+  }
+  Plan* P = &plan->P;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == GS_FP64)
+    return apply_TH<double>(P, P->d, (const double2*)y, (double2*)x, P->perm, st);
+  if (precision == GS_FP32)
+    return apply_TH<float>(P, P->f, (const float2*)y, (float2*)x, P->perm, st);
+  set_error("unknown precision %d", precision);
+  return GS_EINVAL;
+}
+
+gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* opts, gs_solve_info* info,
+                   void* stream) {
+  if (!plan || !x || !y) {
+    set_error("plan, x and y must be non-NULL");
+    return GS_EINVAL;
+  }
+  gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
+  if (opts) o = *opts;
+  if (o.inner_rtol == 0.0) o.inner_rtol = 1e-4;
+  if (!(o.tol > 0.0) || o.maxit < 1 || (o.mode != GS_SOLVE_FP64 && o.mode != GS_SOLVE_MIXED) || o.max_outer < 1 ||
+      !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0)) {
+    set_error("bad solve options (tol > 0, maxit >= 1, mode 0/1, max_outer >= 1, 0 < inner_rtol < 1)");
+    return GS_EINVAL;
+  }
+  return solve(&plan->P, (const double*)y, (double*)x, o, info, (cudaStream_t)stream);
+}
+
+gs_status gs_boundary_constants(int p, double* h, double* UL, double* VL, double* v0L, double* UR, double* VR,
+                                double* v0R) {
+  if (p < 1 || p > GS_MAX_P) {
+    set_error("p = %d outside 1..%d", p, GS_MAX_P);
+    return GS_EINVAL;
+  }
+  Constants c;
+  if (!build_constants(p, &c)) {
+    set_error("boundary construction failed for p = %d", p);
+    return GS_EUNSUPPORTED;
+  }
+  if (h)
+    for (int j = 0; j < 2 * p; ++j) h[j] = c.h[j];
+  if (p == 1) return GS_OK;
+  const EdgeConst* sides[2] = {&c.left, &c.right};
+  double* Us[2] = {UL, UR};
+  double* Vs[2] = {VL, VR};
+  double* v0s[2] = {v0L, v0R};
+  for (int q = 0; q < 2; ++q) {
+    for (int i = 0; i < p; ++i) {
+      if (Us[q])
+        for (int j = 0; j < p; ++j) Us[q][i * p + j] = sides[q]->U[i][j];
+      if (Vs[q])
+        for (int j = 0; j < 2 * p - 1; ++j) Vs[q][i * (2 * p - 1) + j] = sides[q]->V[i][j];
+      if (v0s[q]) v0s[q][i] = sides[q]->v10[i];
+    }
+  }
+  return GS_OK;
+}
+
+const char* gs_strerror(gs_status s) {
+  switch (s) {
+    case GS_OK: return "success";
+    case GS_EINVAL: return "invalid argument";
+    case GS_ENOMEM: return "out of memory";
+    case GS_ECUDA: return "CUDA error";
+    case GS_ENOTCONV: return "not converged";
+    case GS_EBREAKDOWN: return "CGLS breakdown";
+    case GS_ETIMEOUT: return "device wait timed out";
+    case GS_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* gs_last_error_detail(void) { return g_detail; }
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Internal declarations of libgs: plan layout, complex helpers, error handling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gs.h"
+
+#define GS_MAX_P 6
+#define GS_MAX_B (2 * GS_MAX_P)  // boundary columns per dimension (left + right)
+
+namespace gs {
+
+// ------------------------------------------------------------------ host constants
+struct EdgeConst {
+  int p;
+  double U[GS_MAX_P][GS_MAX_P];           // H / sqrt2 (App. A.1)
+  double V[GS_MAX_P][2 * GS_MAX_P - 1];   // h / sqrt2, columns m = p..3p-2
+  double v10[GS_MAX_P];                   // v1(0) = (I - U)^-1 V 1
+  double nest_residual;
+};
+
+struct Constants {
+  int p;
+  double h[2 * GS_MAX_P];  // taps k = -p+1..p at index k + p - 1, sum = 1
+  double mu1, mu2;         // int x phi, int x^2 phi
+  EdgeConst left, right;
+};
+
+bool daubechies_taps(int p, double* h);
+bool build_constants(int p, Constants* c);
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+gs_status cuda_fail(cudaError_t e, const char* what);
+#define GS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return gs::cuda_fail(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------------ complex
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <typename R> using C = typename Cx<R>::T;
+
+// ------------------------------------------------------------------ plan
+constexpr int TILE2 = 16;   // 2D spread tile edge (grid points); >= every KB half-width
+constexpr int TILE1 = 128;  // 1D spread tile length
+constexpr int CHUNK2 = 512; // samples per 2D spread work item (load balance)
+constexpr int CHUNK1 = 512;
+
+// Per-precision device tables and workspaces (R = double or float).
+template <typename R>
+struct PrecData {
+  int m = 0;            // KB half-width (taps per dim 2m)
+  double beta = 0;      // KB shape pi (2 - 1/sigma)
+  // per-sample tables, sorted order
+  R* frac = nullptr;    // [dims][M] fractional grid coordinate in [0, 1)
+  C<R>* w = nullptr;    // [dims][M] interior factor (x factor carries sqrt(mu))
+  C<R>* bf = nullptr;   // [dims][M][2b] boundary factors: left k=0..b-1 then right k=0..b-1
+  R* deap = nullptr;    // [N] 1/psi(k_i) per coefficient index i (interior only)
+  C<R>* tw = nullptr;   // [n/2] exp(-2 pi i k / n)
+  // workspaces
+  C<R>* grid = nullptr;   // n^dims (2D: [lx][ly])
+  C<R>* hbuf = nullptr;   // 2D: N x n, row j of the x transform ([j][lx])
+  C<R>* side = nullptr;   // 2D: [2][2b][n]  (0: x-sides along y, 1: y-sides along x)
+  C<R>* part = nullptr;   // spread partials, per work item
+  C<R>* corner = nullptr; // 2D: (2b)^2 corner adjoint, 1D: 2b boundary adjoint
+  int64_t part_stride = 0;
+  // solver vectors (sorted order for M-vectors)
+  C<R>* vx = nullptr;  // ncoef
+  C<R>* vs = nullptr;  // ncoef
+  C<R>* vp = nullptr;  // ncoef
+  C<R>* vr = nullptr;  // M
+  C<R>* vq = nullptr;  // M
+  C<R>* vz = nullptr;  // ncoef (T^H q in the normal-equation recursion)
+};
+
+struct Plan {
+  int dims = 1, p = 1, J = 0, b = 0, sigma = 2, direct = 0;
+  int m_hi = 8, m_lo = 4;
+  double bandwidth = 0.0;
+  int64_t M = 0, N = 0, n = 0, ncoef = 0;
+  Constants k;
+  int dev = 0;
+  // binning (sorted order)
+  int32_t* perm = nullptr;   // perm[s] = caller index of sorted sample s
+  int32_t* fl = nullptr;     // [dims][M] floor of the grid coordinate (mod n)
+  double* xi_sorted = nullptr; // [dims][M] frequencies (direct mode, tables)
+  int nbx = 0, nby = 0, nbins = 0, tile = 0;
+  int32_t* bin_start = nullptr;  // [nbins + 1] sample range of each bin
+  int32_t* work = nullptr;       // [nwork][3] (bin, s0, s1)
+  int32_t* work_start = nullptr; // [nbins + 1] work items of each bin
+  int nwork = 0;
+  PrecData<double> d;
+  PrecData<float> f;
+  // FP64 scratch for reductions and solver scalars
+  double* red = nullptr;    // partial sums (>= 4096)
+  double* scal = nullptr;   // solver scalars
+  int* flag = nullptr;      // solver stop flag
+  double* y64 = nullptr;    // M, sorted-order data (complex128)
+  double* r64 = nullptr;    // M, FP64 residual (complex128)
+  double* x64 = nullptr;    // ncoef complex128 accumulator
+  cudaStream_t stream = 0;
+};
+
+// implemented in tables.cu
+gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStream_t st);
+// implemented in nfft.cu / direct.cu.  perm != NULL: samples in the caller's
+// order (y[perm[s]]); perm == NULL: samples in the plan's sorted order.
+template <typename R>
+gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st);
+template <typename R>
+gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st);
+template <typename R>
+gs_status direct_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st);
+template <typename R>
+gs_status direct_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st);
+template <typename R>
+inline gs_status apply_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st) {
+  return P->direct ? direct_T<R>(P, D, x, y, perm, st) : nfft_T<R>(P, D, x, y, perm, st);
+}
+template <typename R>
+inline gs_status apply_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st) {
+  return P->direct ? direct_TH<R>(P, D, y, z, perm, st) : nfft_TH<R>(P, D, y, z, perm, st);
+}
+template <typename R>
+gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st);
+template <typename R>
+gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t st);
+// implemented in solve.cu
+gs_status solve(Plan* P, const double* y, double* x, const gs_solve_opts& o, gs_solve_info* info,
+                cudaStream_t st);
+
+inline int ilog2(int64_t n) {
+  int l = 0;
+  while ((int64_t(1) << l) < n) ++l;
+  return l;
+}
+
+}  // namespace gs
+
+struct gs_plan_s {
+  gs::Plan P;
+};

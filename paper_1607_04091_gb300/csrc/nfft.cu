@@ -1,0 +1,740 @@
+// T x and T^H y through the Kaiser-Bessel NFFT plus the boundary factors.
+//
+// Sec. 4: T = [L I R] with I = D F, F the NDFT of eq. NDFT_def on the wrapped
+// frequencies eta' = xi/2^J - round(xi/2^J); Sec. 3.2 / NFFT.jl approximate F x
+// by an NFFT.  Here (window of Kaiser 1974 as used by Keiner-Kunis-Potts):
+//   grid n = sigma N, beta = pi (2 - 1/sigma), half-width m,
+//   g_l   = sum_k c_k / psi(k) exp(-2 pi i k l / n),   psi(k) = I0(m sqrt(beta^2 - (2 pi k/n)^2)),
+//   F c (eta') ~= sum_{|u - l| < m} g_l phi(u - l),   u = n eta',
+//   phi(d) = sinh(beta sqrt(m^2 - d^2)) / (pi sqrt(m^2 - d^2)).
+// The adjoint is the exact transpose: spread with the same window, inverse DFT,
+// divide by psi.  2D (Sec. 5, App. C): separable window and deapodisation;
+// interior x interior through a 2D grid, sides (boundary x interior) through 1D
+// grids of the boundary rows / columns, corners directly.
+//
+// Data layout on the device (per precision R):
+//   grid  [lx][ly]     n x n (2D) or n (1D) oversampled grid
+//   hbuf  [j][lx]      N x n: x-transform of every coefficient row j (2D)
+//   side  [2][2b][n]   forward: x-side grids along y; adjoint: both side grids
+//   part  per spread work item: padded tile, side segments, corner sums
+#include <cstdio>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+namespace {
+
+template <typename R> __device__ inline C<R> mk(R a, R b);
+template <> __device__ inline float2 mk<float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ inline double2 mk<double>(double a, double b) { return make_double2(a, b); }
+
+template <typename T> __device__ inline T cmul(T a, T b) {
+  T r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T> __device__ inline T cmulc(T a, T b) {  // a * conj(b)
+  T r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+template <typename T> __device__ inline T cadd(T a, T b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <typename T, typename R> __device__ inline T cscale(T a, R s) {
+  a.x *= s;
+  a.y *= s;
+  return a;
+}
+
+__device__ inline float kb_window(float d, int m, float beta) {
+  float s2 = (float)(m * m) - d * d;
+  if (s2 <= 0.0f) return beta * 0.318309886183790672f;
+  float s = sqrtf(s2);
+  return sinhf(beta * s) / (3.14159265358979323846f * s);
+}
+__device__ inline double kb_window(double d, int m, double beta) {
+  double s2 = (double)(m * m) - d * d;
+  if (s2 <= 0.0) return beta / M_PI;
+  double s = sqrt(s2);
+  return sinh(beta * s) / (M_PI * s);
+}
+
+__device__ inline int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// In-place radix-2 DIT FFT of nb sequences of length n held in shared memory in
+// bit-reversed order; output in natural order.  tw[k] = exp(-2 pi i k/n).
+template <typename R>
+__device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restrict__ tw, bool inverse) {
+  const int half_total = nb * (n >> 1);
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1);
+    const int step = n >> s;
+    for (int t = threadIdx.x; t < half_total; t += blockDim.x) {
+      int seq = t / (n >> 1);
+      int bt = t - seq * (n >> 1);
+      int grp = bt >> (s - 1);
+      int pos = bt & (half - 1);
+      int i0 = seq * n + grp * 2 * half + pos;
+      int i1 = i0 + half;
+      C<R> w = tw[pos * step];
+      if (inverse) w.y = -w.y;
+      C<R> a = buf[i0];
+      C<R> bb = cmul(buf[i1], w);
+      buf[i0] = cadd(a, bb);
+      buf[i1] = mk<R>(a.x - bb.x, a.y - bb.y);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- 1D forward
+// deapodise + zero-pad + FFT: one CTA, n <= 16384 (float) / 8192 (double)
+template <typename R>
+__global__ void k_fwd1d_fft(const C<R>* __restrict__ x, const R* __restrict__ deap, int64_t N, int n,
+                            int logn, const C<R>* __restrict__ tw, C<R>* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = mk<R>(0, 0);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    R dv = deap[i];
+    if (dv != (R)0) {
+      int idx = (int)((i - N / 2 + n) % n);
+      buf[brev(idx, logn)] = cscale(x[i], dv);
+    }
+  }
+  __syncthreads();
+  fft_smem<R>(buf, 1, n, logn, tw, false);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) grid[i] = buf[i];
+}
+
+// KB interpolation + weights + boundary block, one thread per sorted sample
+template <typename R>
+__global__ void k_interp1d(const int32_t* __restrict__ fl, const R* __restrict__ frac,
+                           const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b,
+                           const C<R>* __restrict__ grid, int n, int m, R beta,
+                           const C<R>* __restrict__ x, int64_t N, int64_t M,
+                           const int32_t* __restrict__ perm, C<R>* __restrict__ y) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  int f = fl[s];
+  R t = frac[s];
+  C<R> v = mk<R>(0, 0);
+  for (int a = 0; a < 2 * m; ++a) {
+    int l = f - m + 1 + a;
+    l = (l % n + n) % n;
+    R d = t + (R)(m - 1 - a);
+    R wv = kb_window(d, m, beta);
+    C<R> g = grid[l];
+    v.x += wv * g.x;
+    v.y += wv * g.y;
+  }
+  C<R> out = cmul(w[s], v);
+  for (int k = 0; k < b; ++k) {
+    out = cadd(out, cmul(bf[s * 2 * b + k], x[k]));
+    out = cadd(out, cmul(bf[s * 2 * b + b + k], x[N - 1 - k]));
+  }
+  y[perm ? perm[s] : s] = out;
+}
+
+// ---------------------------------------------------------------- 1D adjoint
+// CTA per work item; one warp per sample at a time, lanes over the taps, each
+// warp with a private padded tile (no atomics, fixed summation order).
+template <typename R>
+__global__ void k_spread1d(const int32_t* __restrict__ work, const int32_t* __restrict__ fl,
+                           const R* __restrict__ frac, const C<R>* __restrict__ w,
+                           const C<R>* __restrict__ bf, int b, const C<R>* __restrict__ u,
+                           const int32_t* __restrict__ perm, int tile, int m, R beta,
+                           C<R>* __restrict__ part, int64_t stride) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* tiles = reinterpret_cast<C<R>*>(smraw);
+  const int PW = tile + 2 * m;
+  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C<R>* my = tiles + wid * (PW + 2 * b);
+  for (int i = lane; i < PW + 2 * b; i += 32) my[i] = mk<R>(0, 0);
+  __syncwarp();
+  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int ox = bin * tile;
+  for (int s = s0 + wid; s < s1; s += nw) {
+    C<R> us = u[perm ? perm[s] : s];
+    C<R> val = cmulc(us, w[s]);
+    int base = fl[s] - ox + 1;  // padded index of tap 0
+    R t = frac[s];
+    for (int a = lane; a < 2 * m; a += 32) {
+      R wv = kb_window(t + (R)(m - 1 - a), m, beta);
+      C<R> c = my[base + a];
+      c.x += wv * val.x;
+      c.y += wv * val.y;
+      my[base + a] = c;
+    }
+    for (int k = lane; k < 2 * b; k += 32) my[PW + k] = cadd(my[PW + k], cmulc(us, bf[(int64_t)s * 2 * b + k]));
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < PW + 2 * b; i += blockDim.x) {
+    C<R> acc = mk<R>(0, 0);
+    for (int q = 0; q < nw; ++q) acc = cadd(acc, tiles[q * (PW + 2 * b) + i]);
+    part[blockIdx.x * stride + i] = acc;
+  }
+}
+
+// grid point gx: sum of all padded tiles that cover it (neighbour bins, wrap)
+template <typename R>
+__global__ void k_reduce1d(const int32_t* __restrict__ work_start, const C<R>* __restrict__ part,
+                           int64_t stride, int nbx, int tile, int m, int n, C<R>* __restrict__ grid) {
+  int gx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gx >= n) return;
+  const int bx = gx / tile, PW = tile + 2 * m;
+  int cand[3], nc = 0;
+  for (int dx = -1; dx <= 1; ++dx) {
+    int nb = ((bx + dx) % nbx + nbx) % nbx;
+    bool dup = false;
+    for (int q = 0; q < nc; ++q) dup |= (cand[q] == nb);
+    if (!dup) cand[nc++] = nb;
+  }
+  C<R> acc = mk<R>(0, 0);
+  for (int c = 0; c < nc; ++c) {
+    int nb = cand[c];
+    int q0 = ((gx - nb * tile + m) % n + n) % n;
+    for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
+      for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + q]);
+  }
+  grid[gx] = acc;
+}
+
+// boundary (or corner) channel sums over all work items
+template <typename R>
+__global__ void k_reduce_chan(const C<R>* __restrict__ part, int64_t stride, int64_t off, int nch,
+                              int nwork, C<R>* __restrict__ out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nch) return;
+  C<R> acc = mk<R>(0, 0);
+  for (int wi = 0; wi < nwork; ++wi) acc = cadd(acc, part[wi * stride + off + c]);
+  out[c] = acc;
+}
+
+// inverse FFT + crop + deapodise + boundary adjoint
+template <typename R>
+__global__ void k_adj1d_fft(const C<R>* __restrict__ grid, const R* __restrict__ deap, int64_t N, int n,
+                            int logn, const C<R>* __restrict__ tw, const C<R>* __restrict__ bsum, int b,
+                            C<R>* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) buf[brev(i, logn)] = grid[i];
+  __syncthreads();
+  fft_smem<R>(buf, 1, n, logn, tw, true);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C<R> v;
+    if (i < b) v = bsum[i];
+    else if (i >= N - b) v = bsum[b + (N - 1 - i)];
+    else v = cscale(buf[(i - N / 2 + n) % n], deap[i]);
+    z[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- 2D forward
+// pass 1: x-transform of every coefficient row j -> hbuf[j][:]
+template <typename R>
+__global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ deap, int N, int n,
+                              int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int j0 = blockIdx.x * rows;
+  const int nr = min(rows, N - j0);
+  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) buf[i] = mk<R>(0, 0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
+    int r = t / N, i = t - r * N;
+    R dv = deap[i];
+    if (dv != (R)0) {
+      int idx = (i - N / 2 + n) % n;
+      buf[r * n + brev(idx, logn)] = cscale(x[(int64_t)(j0 + r) * N + i], dv);
+    }
+  }
+  __syncthreads();
+  fft_smem<R>(buf, nr, n, logn, tw, false);
+  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) hbuf[(int64_t)j0 * n + t] = buf[t];
+}
+
+// pass 2: y-transform of hbuf columns (interior rows) -> grid[lx][:], and of the
+// x-boundary coefficient rows i in B -> side[0][k][:]
+template <typename R>
+__global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restrict__ x,
+                              const R* __restrict__ deap, int N, int n, int logn, int b, int cols,
+                              const C<R>* __restrict__ tw, C<R>* __restrict__ grid, C<R>* __restrict__ side) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int c0 = blockIdx.x * cols;
+  const int ntot = n + 2 * b;
+  const int nc = min(cols, ntot - c0);
+  for (int i = threadIdx.x; i < nc * n; i += blockDim.x) buf[i] = mk<R>(0, 0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc * N; t += blockDim.x) {
+    int j = t / nc, c = t - j * nc;
+    R dv = deap[j];
+    if (dv == (R)0) continue;
+    int col = c0 + c;
+    C<R> v;
+    if (col < n) {
+      v = hbuf[(int64_t)j * n + col];
+    } else {
+      int k = col - n;
+      int i = (k < b) ? k : (N - 1 - (k - b));
+      v = x[(int64_t)j * N + i];
+    }
+    int idx = (j - N / 2 + n) % n;
+    buf[c * n + brev(idx, logn)] = cscale(v, dv);
+  }
+  __syncthreads();
+  fft_smem<R>(buf, nc, n, logn, tw, false);
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    int c = t / n, l = t - c * n;
+    int col = c0 + c;
+    if (col < n) grid[(int64_t)col * n + l] = buf[t];
+    else side[(int64_t)(col - n) * n + l] = buf[t];
+  }
+}
+
+// interpolation + factors + sides + corners, one thread per sorted sample
+template <typename R>
+__global__ void k_interp2d(const int32_t* __restrict__ fl, const R* __restrict__ frac,
+                           const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b,
+                           const C<R>* __restrict__ grid, const C<R>* __restrict__ hbuf,
+                           const C<R>* __restrict__ side, int n, int m, R beta,
+                           const C<R>* __restrict__ x, int N, int64_t M,
+                           const int32_t* __restrict__ perm, C<R>* __restrict__ y) {
+  __shared__ C<R> xc[GS_MAX_B * GS_MAX_B];
+  const int b2 = 2 * b;
+  for (int t = threadIdx.x; t < b2 * b2; t += blockDim.x) {
+    int kx = t % b2, ky = t / b2;
+    int i = (kx < b) ? kx : N - 1 - (kx - b);
+    int j = (ky < b) ? ky : N - 1 - (ky - b);
+    xc[t] = x[(int64_t)j * N + i];
+  }
+  __syncthreads();
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= M) return;
+  const int fx = fl[s], fy = fl[M + s];
+  const R tx = frac[s], ty = frac[M + s];
+  R wx[32], wy[32];
+  for (int a = 0; a < 2 * m; ++a) {
+    wx[a] = kb_window(tx + (R)(m - 1 - a), m, beta);
+    wy[a] = kb_window(ty + (R)(m - 1 - a), m, beta);
+  }
+  int ly[32];
+  for (int c = 0; c < 2 * m; ++c) ly[c] = ((fy - m + 1 + c) % n + n) % n;
+  C<R> vi = mk<R>(0, 0);
+  for (int a = 0; a < 2 * m; ++a) {
+    int lx = ((fx - m + 1 + a) % n + n) % n;
+    const C<R>* row = grid + (int64_t)lx * n;
+    C<R> acc = mk<R>(0, 0);
+    for (int c = 0; c < 2 * m; ++c) {
+      C<R> g = row[ly[c]];
+      acc.x += wy[c] * g.x;
+      acc.y += wy[c] * g.y;
+    }
+    vi.x += wx[a] * acc.x;
+    vi.y += wx[a] * acc.y;
+  }
+  const C<R> wxs = w[s], wys = w[M + s];
+  C<R> out = cmul(cmul(wxs, wys), vi);
+  if (b > 0) {
+    const C<R>* bx = bf + s * b2;
+    const C<R>* by = bf + (M + s) * b2;
+    C<R> sx = mk<R>(0, 0), sy = mk<R>(0, 0);
+    for (int k = 0; k < b2; ++k) {
+      // x-side k: 1D grid along y
+      const C<R>* g0 = side + (int64_t)k * n;
+      C<R> a0 = mk<R>(0, 0);
+      for (int c = 0; c < 2 * m; ++c) {
+        C<R> g = g0[ly[c]];
+        a0.x += wy[c] * g.x;
+        a0.y += wy[c] * g.y;
+      }
+      sx = cadd(sx, cmul(bx[k], a0));
+      // y-side k: row j = B(k) of the x transform, along x
+      int j = (k < b) ? k : N - 1 - (k - b);
+      const C<R>* g1 = hbuf + (int64_t)j * n;
+      C<R> a1 = mk<R>(0, 0);
+      for (int a = 0; a < 2 * m; ++a) {
+        int lx = ((fx - m + 1 + a) % n + n) % n;
+        C<R> g = g1[lx];
+        a1.x += wx[a] * g.x;
+        a1.y += wx[a] * g.y;
+      }
+      sy = cadd(sy, cmul(by[k], a1));
+    }
+    out = cadd(out, cmul(wys, sx));
+    out = cadd(out, cmul(wxs, sy));
+    C<R> cc = mk<R>(0, 0);
+    for (int ky = 0; ky < b2; ++ky) {
+      C<R> r = mk<R>(0, 0);
+      for (int kx = 0; kx < b2; ++kx) r = cadd(r, cmul(bx[kx], xc[ky * b2 + kx]));
+      cc = cadd(cc, cmul(by[ky], r));
+    }
+    out = cadd(out, cc);
+  }
+  y[perm ? perm[s] : s] = out;
+}
+
+// ---------------------------------------------------------------- 2D adjoint
+// Spread of one work item (tile (bx, by), samples s0..s1): per warp a private
+// padded tile P[(T+2m)^2] ([px][py]), x-side segments S0[2b][T+2m] (along y),
+// y-side segments S1[2b][T+2m] (along x), corner sums in registers.
+template <typename R>
+__global__ void k_spread2d(const int32_t* __restrict__ work, const int32_t* __restrict__ fl,
+                           const R* __restrict__ frac, const C<R>* __restrict__ w,
+                           const C<R>* __restrict__ bf, int b, const C<R>* __restrict__ u,
+                           const int32_t* __restrict__ perm, int64_t M, int nbx, int tile, int m,
+                           R beta, C<R>* __restrict__ part, int64_t stride) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int PW = tile + 2 * m;
+  const int b2 = 2 * b;
+  const int wsz = PW * PW + 2 * b2 * PW + b2 * b2;  // P | S0 | S1 | corners
+  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C<R>* my = reinterpret_cast<C<R>*>(smraw) + (int64_t)wid * wsz;
+  R* wins = reinterpret_cast<R*>(reinterpret_cast<C<R>*>(smraw) + (int64_t)nw * wsz) + wid * 64;
+  C<R>* P = my;
+  C<R>* S0 = my + PW * PW;
+  C<R>* S1 = S0 + b2 * PW;
+  C<R>* CC = S1 + b2 * PW;
+  for (int i = lane; i < wsz; i += 32) my[i] = mk<R>(0, 0);
+  __syncwarp();
+  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int ox = (bin % nbx) * tile, oy = (bin / nbx) * tile;
+  const int tw = 2 * m;
+  for (int s = s0 + wid; s < s1; s += nw) {
+    const C<R> us = u[perm ? perm[s] : s];
+    const int px = fl[s] - ox + 1, py = fl[M + s] - oy + 1;
+    const R tx = frac[s], ty = frac[M + s];
+    for (int q = lane; q < 2 * tw; q += 32)
+      wins[q] = (q < tw) ? kb_window(tx + (R)(m - 1 - q), m, beta) : kb_window(ty + (R)(m - 1 - (q - tw)), m, beta);
+    __syncwarp();
+    const C<R> wxs = w[s], wys = w[M + s];
+    const C<R> vi = cmulc(cmulc(us, wxs), wys);
+    for (int t = lane; t < tw * tw; t += 32) {
+      int a = t / tw, c = t - a * tw;
+      R wv = wins[a] * wins[tw + c];
+      C<R>& dst = P[(px + a) * PW + (py + c)];
+      dst.x += wv * vi.x;
+      dst.y += wv * vi.y;
+    }
+    if (b > 0) {
+      const C<R>* bx = bf + s * b2;
+      const C<R>* by = bf + (M + s) * b2;
+      for (int t = lane; t < b2 * tw; t += 32) {
+        int k = t / tw, c = t - k * tw;
+        C<R> v0 = cmulc(cmulc(us, bx[k]), wys);  // x-side k, along y
+        C<R>& d0 = S0[k * PW + py + c];
+        R w0 = wins[tw + c];
+        d0.x += w0 * v0.x;
+        d0.y += w0 * v0.y;
+        C<R> v1 = cmulc(cmulc(us, wxs), by[k]);  // y-side k, along x
+        C<R>& d1 = S1[k * PW + px + c];
+        R w1 = wins[c];
+        d1.x += w1 * v1.x;
+        d1.y += w1 * v1.y;
+      }
+      for (int ch = lane; ch < b2 * b2; ch += 32) {
+        int kx = ch % b2, ky = ch / b2;
+        CC[ch] = cadd(CC[ch], cmulc(cmulc(us, bx[kx]), by[ky]));
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  C<R>* out = part + blockIdx.x * stride;
+  const C<R>* all = reinterpret_cast<C<R>*>(smraw);
+  for (int i = threadIdx.x; i < wsz; i += blockDim.x) {
+    C<R> acc = mk<R>(0, 0);
+    for (int q = 0; q < nw; ++q) acc = cadd(acc, all[(int64_t)q * wsz + i]);
+    out[i] = acc;
+  }
+}
+
+__device__ inline int neighbours(int bx, int nbx, int* cand) {
+  int nc = 0;
+  for (int dx = -1; dx <= 1; ++dx) {
+    int nb = ((bx + dx) % nbx + nbx) % nbx;
+    bool dup = false;
+    for (int q = 0; q < nc; ++q) dup |= (cand[q] == nb);
+    if (!dup) cand[nc++] = nb;
+  }
+  return nc;
+}
+
+// 2D grid point (gx, gy): sum of the padded tiles of the neighbouring bins
+template <typename R>
+__global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<R>* __restrict__ part,
+                                int64_t stride, int nbx, int tile, int m, int n, C<R>* __restrict__ grid) {
+  const int gx = blockIdx.x * tile + threadIdx.y;
+  const int gy = blockIdx.y * tile + threadIdx.x;
+  if (gx >= n || gy >= n) return;
+  const int PW = tile + 2 * m;
+  int cx[3], cy[3];
+  int ncx = neighbours(gx / tile, nbx, cx), ncy = neighbours(gy / tile, nbx, cy);
+  C<R> acc = mk<R>(0, 0);
+  for (int iy = 0; iy < ncy; ++iy)
+    for (int ix = 0; ix < ncx; ++ix) {
+      int nb = cy[iy] * nbx + cx[ix];
+      int qx0 = ((gx - cx[ix] * tile + m) % n + n) % n;
+      int qy0 = ((gy - cy[iy] * tile + m) % n + n) % n;
+      for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
+        for (int qx = qx0; qx < PW; qx += n)
+          for (int qy = qy0; qy < PW; qy += n) acc = cadd(acc, part[wi * stride + qx * PW + qy]);
+    }
+  grid[(int64_t)gx * n + gy] = acc;
+}
+
+// side grids: which = 0 -> x-side k along y (segments S0, bins grouped by row),
+// which = 1 -> y-side k along x (segments S1, bins grouped by column)
+template <typename R>
+__global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const C<R>* __restrict__ part,
+                                int64_t stride, int nbx, int tile, int m, int n, int b2,
+                                C<R>* __restrict__ side) {
+  const int which = blockIdx.z;
+  const int k = blockIdx.y;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int PW = tile + 2 * m;
+  const int64_t off = (int64_t)PW * PW + (int64_t)which * b2 * PW + (int64_t)k * PW;
+  int cn[3];
+  int nc = neighbours(g / tile, nbx, cn);
+  C<R> acc = mk<R>(0, 0);
+  for (int ci = 0; ci < nc; ++ci) {
+    int q0 = ((g - cn[ci] * tile + m) % n + n) % n;
+    for (int o = 0; o < nbx; ++o) {
+      int nb = (which == 0) ? (cn[ci] * nbx + o) : (o * nbx + cn[ci]);
+      for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
+        for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + off + q]);
+    }
+  }
+  side[((int64_t)which * b2 + k) * n + g] = acc;
+}
+
+// adjoint pass 2: inverse y-transform of grid columns -> hbuf[j][lx] (interior j),
+// and of the x-side grids -> z[i + N j] for i in B, j interior
+template <typename R>
+__global__ void k_adj2d_pass2(const C<R>* __restrict__ grid, const C<R>* __restrict__ side,
+                              const R* __restrict__ deap, int N, int n, int logn, int b, int cols,
+                              const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf, C<R>* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int c0 = blockIdx.x * cols;
+  const int ntot = n + 2 * b;
+  const int nc = min(cols, ntot - c0);
+  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
+    int c = t / n, l = t - c * n;
+    int col = c0 + c;
+    C<R> v = (col < n) ? grid[(int64_t)col * n + l] : side[(int64_t)(col - n) * n + l];
+    buf[c * n + brev(l, logn)] = v;
+  }
+  __syncthreads();
+  fft_smem<R>(buf, nc, n, logn, tw, true);
+  for (int t = threadIdx.x; t < nc * N; t += blockDim.x) {
+    int j = t / nc, c = t - j * nc;
+    R dv = deap[j];
+    if (dv == (R)0) continue;
+    int col = c0 + c;
+    C<R> v = cscale(buf[c * n + (j - N / 2 + n) % n], dv);
+    if (col < n) {
+      hbuf[(int64_t)j * n + col] = v;
+    } else {
+      int k = col - n;
+      int i = (k < b) ? k : (N - 1 - (k - b));
+      z[(int64_t)j * N + i] = v;
+    }
+  }
+}
+
+// adjoint pass 1: inverse x-transform of hbuf rows (interior j) or of the y-side
+// grids (boundary j) -> z[i + N j] for interior i; corners for boundary i and j
+template <typename R>
+__global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restrict__ side1,
+                              const C<R>* __restrict__ corner, const R* __restrict__ deap, int N,
+                              int n, int logn, int b, int rows, const C<R>* __restrict__ tw,
+                              C<R>* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int j0 = blockIdx.x * rows;
+  const int nr = min(rows, N - j0);
+  const int b2 = 2 * b;
+  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
+    int r = t / n, l = t - r * n;
+    int j = j0 + r;
+    C<R> v;
+    if (j >= b && j < N - b) {
+      v = hbuf[(int64_t)j * n + l];
+    } else {
+      int k = (j < b) ? j : b + (N - 1 - j);
+      v = side1[(int64_t)k * n + l];
+    }
+    buf[r * n + brev(l, logn)] = v;
+  }
+  __syncthreads();
+  fft_smem<R>(buf, nr, n, logn, tw, true);
+  for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
+    int r = t / N, i = t - r * N;
+    int j = j0 + r;
+    R dv = deap[i];
+    C<R> v;
+    if (dv != (R)0) {
+      v = cscale(buf[r * n + (i - N / 2 + n) % n], dv);
+    } else {
+      bool jb = (j < b) || (j >= N - b);
+      if (!jb) continue;  // x-side entries come from pass 2
+      int kx = (i < b) ? i : b + (N - 1 - i);
+      int ky = (j < b) ? j : b + (N - 1 - j);
+      v = corner[ky * b2 + kx];
+    }
+    z[(int64_t)j * N + i] = v;
+  }
+}
+
+template <typename R>
+__global__ void k_gather(const C<R>* __restrict__ in, const int32_t* __restrict__ perm, int64_t M,
+                         C<R>* __restrict__ out) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s < M) out[s] = in[perm[s]];
+}
+template <typename R>
+__global__ void k_scatter(const C<R>* __restrict__ in, const int32_t* __restrict__ perm, int64_t M,
+                          C<R>* __restrict__ out) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s < M) out[perm[s]] = in[s];
+}
+
+template <typename R>
+gs_status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return GS_OK;
+}
+
+template <typename R> constexpr int pass_cols() { return sizeof(R) == 4 ? 8 : 4; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host drivers
+template <typename R>
+gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st) {
+  const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b;
+  const int64_t M = P->M;
+  const R beta = (R)D.beta;
+  if (P->dims == 1) {
+    size_t sh = (size_t)n * sizeof(C<R>);
+    if (sh > 227 * 1024) {
+      set_error("1D grid of %d points does not fit one CTA in this precision", n);
+      return GS_EUNSUPPORTED;
+    }
+    gs_status s = set_smem<R>((const void*)k_fwd1d_fft<R>, sh);
+    if (s != GS_OK) return s;
+    k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid);
+    k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta, x, N,
+                                                   M, perm, y);
+  } else {
+    const int rows = 2;
+    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+    gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
+    if (s != GS_OK) return s;
+    k_fwd2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw, D.hbuf);
+    const int cols = pass_cols<R>();
+    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
+    s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
+    if (s != GS_OK) return s;
+    k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b, cols,
+                                                                      D.tw, D.grid, D.side);
+    k_interp2d<R><<<(M + 127) / 128, 128, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, D.hbuf, D.side, n, D.m,
+                                                   beta, x, N, M, perm, y);
+  }
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+template <typename R>
+gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st) {
+  const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
+  const int64_t M = P->M;
+  const R beta = (R)D.beta;
+  const int m = D.m, tile = P->tile;
+  if (P->nwork == 0) {
+    GS_CUDA(cudaMemsetAsync(z, 0, P->ncoef * sizeof(C<R>), st));
+    return GS_OK;
+  }
+  if (P->dims == 1) {
+    const int warps = 4;
+    size_t sh = (size_t)warps * (tile + 2 * m + b2) * sizeof(C<R>);
+    k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile, m,
+                                                     beta, D.part, D.part_stride);
+    k_reduce1d<R><<<(n + 127) / 128, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
+                                                   D.grid);
+    if (b2 > 0)
+      k_reduce_chan<R><<<1, 32, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner);
+    size_t shf = (size_t)n * sizeof(C<R>);
+    gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
+    if (s != GS_OK) return s;
+    k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z);
+  } else {
+    const int warps = 4;
+    const int PW = tile + 2 * m;
+    const int wsz = PW * PW + 2 * b2 * PW + b2 * b2;
+    size_t sh = (size_t)warps * wsz * sizeof(C<R>) + (size_t)warps * 64 * sizeof(R);
+    gs_status s = set_smem<R>((const void*)k_spread2d<R>, sh);
+    if (s != GS_OK) return s;
+    k_spread2d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, M, P->nbx,
+                                                     tile, m, beta, D.part, D.part_stride);
+    dim3 rg(P->nbx, P->nby), rb(tile, tile);
+    k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n, D.grid);
+    if (b2 > 0) {
+      dim3 sg((n + 127) / 128, b2, 2);
+      k_reduce2d_side<R><<<sg, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n, b2,
+                                              D.side);
+      k_reduce_chan<R><<<(b2 * b2 + 63) / 64, 64, 0, st>>>(D.part, D.part_stride, wsz - b2 * b2, b2 * b2,
+                                                            P->nwork, D.corner);
+    }
+    const int cols = pass_cols<R>();
+    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
+    s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
+    if (s != GS_OK) return s;
+    k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b, cols,
+                                                                    D.tw, D.hbuf, z);
+    const int rows = 2;
+    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+    s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
+    if (s != GS_OK) return s;
+    k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n, D.corner,
+                                                               D.deap, N, n, logn, b, rows, D.tw, z);
+  }
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+template <typename R>
+gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st) {
+  k_gather<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_user, P->perm, P->M, y_sorted);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+template <typename R>
+gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t st) {
+  k_scatter<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_sorted, P->perm, P->M, y_user);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
+template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t);
+template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
+template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,
+                                   cudaStream_t);
+template gs_status gather_sorted<float>(Plan*, const float2*, float2*, cudaStream_t);
+template gs_status gather_sorted<double>(Plan*, const double2*, double2*, cudaStream_t);
+template gs_status scatter_user<float>(Plan*, const float2*, float2*, cudaStream_t);
+template gs_status scatter_user<double>(Plan*, const double2*, double2*, cudaStream_t);
+
+}  // namespace gs

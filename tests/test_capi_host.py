@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+function include/gs.h declares, validates arguments before touching CUDA, and
+its plan-time constants match the oracle's independent construction."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1607_04091_gb300 as gs
+from oracle.boundary import EdgeSide
+from oracle.filters import daubechies_filter
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gs.h")
+
+
+def declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:gs_status|void|const char\*)\s+(gs_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = gs.load()
+    names = declared()
+    assert "gs_apply_T" in names and "gs_solve" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(gs.EXPORTS) | set(names)
+
+
+def test_strerror_and_codes():
+    lib = gs.load()
+    assert lib.gs_strerror(gs.GS_OK) == b"success"
+    assert lib.gs_strerror(gs.GS_ENOTCONV) == b"not converged"
+    assert lib.gs_strerror(99) == b"unknown status"
+
+
+@pytest.mark.parametrize("kw", [dict(p=0, J=6), dict(p=7, J=6), dict(p=4, J=2), dict(p=2, J=0)])
+def test_plan_rejects_bad_sizes_without_gpu(kw):
+    xi = np.linspace(-10, 10, 50)
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(xi, kw["p"], kw["J"], stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+
+
+def test_plan_rejects_nonfinite_xi_and_weights():
+    xi = np.linspace(-10, 10, 50)
+    xi[3] = np.nan
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(xi, 2, 5, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+    xi = np.linspace(-10, 10, 50)
+    w = np.ones(50)
+    w[7] = -1
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(xi, 2, 5, weights=w, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_2d(np.zeros((10, 2)), 2, 5, stream=_NoStream(), sigma=3)
+    assert e.value.status == gs.GS_EINVAL
+
+
+class _NoStream:
+    cuda_stream = 0
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_host_constants_match_oracle(p):
+    c = gs.gs_boundary_constants(p)
+    k, h = daubechies_filter(p)
+    assert np.max(np.abs(c["h"] - h)) < 1e-15
+    if p == 1:
+        return
+    tol = 1e-12 if p <= 4 else 1e-10  # the edge construction loses digits as p grows
+    for side in ["left", "right"]:
+        e = EdgeSide(p, side)
+        assert np.max(np.abs(c["U_" + side] - e.U)) < tol
+        assert np.max(np.abs(c["V_" + side] - e.V)) < tol
+        assert np.max(np.abs(c["v0_" + side] - e.v1_0)) < 10 * tol
