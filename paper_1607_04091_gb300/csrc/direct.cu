@@ -99,16 +99,16 @@ __global__ void k_direct_TH(const double* __restrict__ xs, const C<R>* __restric
 
 template <typename R>
 gs_status direct_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st) {
-  k_direct_T<R><<<(P->M + 127) / 128, 128, 0, st>>>(P->xi_sorted, D.w, D.bf, P->M, (int)P->N, P->J, P->b,
-                                                    P->dims, x, perm, y);
+  GS_LAUNCH(pname<R>("direct_T<f32>", "direct_T<f64>"), st, k_direct_T<R><<<(P->M + 127) / 128, 128, 0, st>>>(P->xi_sorted, D.w, D.bf, P->M, (int)P->N, P->J, P->b,
+                                                    P->dims, x, perm, y));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
 
 template <typename R>
 gs_status direct_TH(Plan* P, PrecData<R>& D, const C<R>* u, C<R>* z, const int32_t* perm, cudaStream_t st) {
-  k_direct_TH<R><<<(P->ncoef + 127) / 128, 128, 0, st>>>(P->xi_sorted, D.w, D.bf, P->M, (int)P->N, P->J, P->b,
-                                                         P->dims, u, perm, z);
+  GS_LAUNCH(pname<R>("direct_TH<f32>", "direct_TH<f64>"), st, k_direct_TH<R><<<(P->ncoef + 127) / 128, 128, 0, st>>>(P->xi_sorted, D.w, D.bf, P->M, (int)P->N, P->J, P->b,
+                                                         P->dims, u, perm, z));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

@@ -41,6 +41,23 @@ gs_status cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return gs::cuda_fail(e_, #call); \
   } while (0)
 
+// ------------------------------------------------------------------ tracing
+// When enabled (gs_profile), every wrapped launch records a CUDA event pair on
+// its stream; gs_profile_report aggregates them per kernel name.
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+bool prof_on();
+#define GS_LAUNCH(name, st, ...)            \
+  do {                                      \
+    const bool p_ = gs::prof_on();          \
+    if (p_) gs::prof_begin((name), (st));   \
+    __VA_ARGS__;                            \
+    if (p_) gs::prof_end((st));             \
+  } while (0)
+template <typename R> constexpr const char* pname(const char* f32, const char* f64) {
+  return sizeof(R) == 4 ? f32 : f64;
+}
+
 // ------------------------------------------------------------------ complex
 template <typename R> struct Cx;
 template <> struct Cx<float> { using T = float2; };

@@ -634,23 +634,29 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     }
     gs_status s = set_smem<R>((const void*)k_fwd1d_fft<R>, sh);
     if (s != GS_OK) return s;
-    k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid);
-    k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta, x, N,
-                                                   M, perm, y);
+    GS_LAUNCH(pname<R>("fwd1d_fft<f32>", "fwd1d_fft<f64>"), st,
+              k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
+    GS_LAUNCH(pname<R>("interp1d<f32>", "interp1d<f64>"), st,
+              k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
+                                                             x, N, M, perm, y));
   } else {
     const int rows = 2;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
-    k_fwd2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw, D.hbuf);
+    GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
+              k_fwd2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw,
+                                                                        D.hbuf));
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
-    k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b, cols,
-                                                                      D.tw, D.grid, D.side);
-    k_interp2d<R><<<(M + 127) / 128, 128, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, D.hbuf, D.side, n, D.m,
-                                                   beta, x, N, M, perm, y);
+    GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
+              k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
+                                                                                cols, D.tw, D.grid, D.side));
+    GS_LAUNCH(pname<R>("interp2d<f32>", "interp2d<f64>"), st,
+              k_interp2d<R><<<(M + 127) / 128, 128, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, D.hbuf, D.side, n,
+                                                             D.m, beta, x, N, M, perm, y));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -669,16 +675,20 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
   if (P->dims == 1) {
     const int warps = 4;
     size_t sh = (size_t)warps * (tile + 2 * m + b2) * sizeof(C<R>);
-    k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile, m,
-                                                     beta, D.part, D.part_stride);
-    k_reduce1d<R><<<(n + 127) / 128, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
-                                                   D.grid);
+    GS_LAUNCH(pname<R>("spread1d<f32>", "spread1d<f64>"), st,
+              k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile,
+                                                              m, beta, D.part, D.part_stride));
+    GS_LAUNCH(pname<R>("reduce1d<f32>", "reduce1d<f64>"), st,
+              k_reduce1d<R><<<(n + 127) / 128, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m,
+                                                             n, D.grid));
     if (b2 > 0)
-      k_reduce_chan<R><<<1, 32, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner);
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
+                k_reduce_chan<R><<<1, 32, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
     size_t shf = (size_t)n * sizeof(C<R>);
     gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
     if (s != GS_OK) return s;
-    k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z);
+    GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
+              k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
   } else {
     const int warps = 4;
     const int PW = tile + 2 * m;
@@ -686,29 +696,37 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     size_t sh = (size_t)warps * wsz * sizeof(C<R>) + (size_t)warps * 64 * sizeof(R);
     gs_status s = set_smem<R>((const void*)k_spread2d<R>, sh);
     if (s != GS_OK) return s;
-    k_spread2d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, M, P->nbx,
-                                                     tile, m, beta, D.part, D.part_stride);
+    GS_LAUNCH(pname<R>("spread2d<f32>", "spread2d<f64>"), st,
+              k_spread2d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, M,
+                                                              P->nbx, tile, m, beta, D.part, D.part_stride));
     dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n, D.grid);
+    GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+              k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
+                                                    D.grid));
     if (b2 > 0) {
       dim3 sg((n + 127) / 128, b2, 2);
-      k_reduce2d_side<R><<<sg, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n, b2,
-                                              D.side);
-      k_reduce_chan<R><<<(b2 * b2 + 63) / 64, 64, 0, st>>>(D.part, D.part_stride, wsz - b2 * b2, b2 * b2,
-                                                            P->nwork, D.corner);
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
+                k_reduce2d_side<R><<<sg, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
+                                                        b2, D.side));
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
+                k_reduce_chan<R><<<(b2 * b2 + 63) / 64, 64, 0, st>>>(D.part, D.part_stride, wsz - b2 * b2,
+                                                                      b2 * b2, P->nwork, D.corner));
     }
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
-    k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b, cols,
-                                                                    D.tw, D.hbuf, z);
+    GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
+              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
+                                                                              cols, D.tw, D.hbuf, z));
     const int rows = 2;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
-    k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n, D.corner,
-                                                               D.deap, N, n, logn, b, rows, D.tw, z);
+    GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+                                                                         D.corner, D.deap, N, n, logn, b, rows,
+                                                                         D.tw, z));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -716,13 +734,13 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
 
 template <typename R>
 gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st) {
-  k_gather<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_user, P->perm, P->M, y_sorted);
+  GS_LAUNCH(pname<R>("gather<f32>", "gather<f64>"), st, k_gather<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_user, P->perm, P->M, y_sorted));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
 template <typename R>
 gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t st) {
-  k_scatter<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_sorted, P->perm, P->M, y_user);
+  GS_LAUNCH(pname<R>("scatter<f32>", "scatter<f64>"), st, k_scatter<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_sorted, P->perm, P->M, y_user));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

@@ -162,8 +162,8 @@ inline int grid_for(int64_t n) {
 
 template <typename R>
 gs_status norm2_into(Plan* P, const C<R>* v, int64_t n, int slot, const int* flag, cudaStream_t st) {
-  k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(v, n, P->red, flag);
-  k_store<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, slot, flag);
+  GS_LAUNCH("solve_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(v, n, P->red, flag));
+  GS_LAUNCH("solve_store", st, k_store<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, slot, flag));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -178,8 +178,8 @@ gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, 
                     int* iters, int* stop) {
   const int64_t nc = P->ncoef, M = P->M;
   GS_CUDA(cudaMemsetAsync(D.vx, 0, nc * sizeof(C<R>), st));
-  k_copy<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc);
-  k_init_pass<<<1, 1, 0, st>>>(P->scal, P->flag, thr2, (double)maxit);
+  GS_LAUNCH("solve_copy", st, k_copy<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc));
+  GS_LAUNCH("solve_init_pass", st, k_init_pass<<<1, 1, 0, st>>>(P->scal, P->flag, thr2, (double)maxit));
   GS_CUDA(cudaGetLastError());
   int hflag = F_RUN;
   double hit = 0;
@@ -192,21 +192,27 @@ gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, 
     for (int k = 0; k < check; ++k) {
       gs_status s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
       if (s != GS_OK) return s;
-      k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag);
-      k_alpha<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag);
+      GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
+      GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
       if (normal_eq) {
-        k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(D.vx, D.vp, nc, nullptr, nullptr, 0, P->scal, P->flag);
+        GS_LAUNCH("cgls_axpy", st,
+                  k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(D.vx, D.vp, nc, nullptr, nullptr, 0, P->scal,
+                                                               P->flag));
         s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
         if (s != GS_OK) return s;
-        k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(nullptr, nullptr, 0, D.vs, D.vz, nc, P->scal, P->flag);
+        GS_LAUNCH("cgls_axpy", st,
+                  k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(nullptr, nullptr, 0, D.vs, D.vz, nc, P->scal,
+                                                               P->flag));
       } else {
-        k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal, P->flag);
+        GS_LAUNCH("cgls_axpy", st,
+                  k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal,
+                                                                   P->flag));
         s = apply_TH<R>(P, D, D.vr, D.vs, nullptr, st);
         if (s != GS_OK) return s;
       }
-      k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vs, nc, P->red, P->flag);
-      k_beta<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag);
-      k_update_p<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc, P->scal, P->flag);
+      GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vs, nc, P->red, P->flag));
+      GS_LAUNCH("cgls_scalar", st, k_beta<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
+      GS_LAUNCH("cgls_axpy", st, k_update_p<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc, P->scal, P->flag));
       GS_CUDA(cudaGetLastError());
       ++done;
     }
@@ -235,7 +241,7 @@ __global__ void k_addto(double2* __restrict__ x, const C<R>* __restrict__ d, int
 // r64 = y64 - T x64 (float64 forward apply)
 gs_status residual64(Plan* P, cudaStream_t st) {
   GS_TRY(apply_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, st));
-  k_sub64<<<grid_for(P->M), 256, 0, st>>>((double2*)P->r64, (const double2*)P->y64, P->d.vq, P->M);
+  GS_LAUNCH("solve_sub64", st, k_sub64<<<grid_for(P->M), 256, 0, st>>>((double2*)P->r64, (const double2*)P->y64, P->d.vq, P->M));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -246,13 +252,13 @@ template <typename R>
 gs_status adjoint_of_residual(Plan* P, PrecData<R>& D, cudaStream_t st);
 template <>
 gs_status adjoint_of_residual<double>(Plan* P, PrecData<double>& D, cudaStream_t st) {
-  k_copy<double><<<grid_for(P->M), 256, 0, st>>>(D.vr, (const double2*)P->r64, P->M);
+  GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(P->M), 256, 0, st>>>(D.vr, (const double2*)P->r64, P->M));
   GS_TRY(apply_TH<double>(P, D, D.vr, D.vs, nullptr, st));
   return norm2_into<double>(P, D.vs, P->ncoef, S_TMP, nullptr, st);
 }
 template <>
 gs_status adjoint_of_residual<float>(Plan* P, PrecData<float>& D, cudaStream_t st) {
-  k_to32<<<grid_for(P->M), 256, 0, st>>>(D.vr, (const double2*)P->r64, P->M);
+  GS_LAUNCH("solve_to32", st, k_to32<<<grid_for(P->M), 256, 0, st>>>(D.vr, (const double2*)P->r64, P->M));
   GS_TRY(apply_TH<float>(P, D, D.vr, D.vs, nullptr, st));
   return norm2_into<float>(P, D.vs, P->ncoef, S_TMP, nullptr, st);
 }
@@ -280,7 +286,7 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
   if (err != GS_OK) return err;
   // ||T^H y||^2, the scale of the stop test
   GS_CUDA(cudaMemsetAsync(x64, 0, nc * sizeof(double2), st));
-  k_copy<double><<<grid_for(M), 256, 0, st>>>((double2*)P->r64, y64, M);
+  GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(M), 256, 0, st>>>((double2*)P->r64, y64, M));
   if (o.mode == GS_SOLVE_FP64 || o.tol < 1e-7) GS_TRY(adjoint_of_residual<double>(P, P->d, st));
   else GS_TRY(adjoint_of_residual<float>(P, P->f, st));
   const double hb2 = read_scal(P, S_TMP, st, &err);
@@ -294,7 +300,7 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
   }
   const double thr2 = o.tol * o.tol * hb2;
   if (o.x0_given) {
-    k_copy<double><<<grid_for(nc), 256, 0, st>>>(x64, (const double2*)x_user, nc);
+    GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(nc), 256, 0, st>>>(x64, (const double2*)x_user, nc));
     GS_TRY(residual64(P, st));
   }
   const int check = 4;
@@ -304,7 +310,7 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
     if (o.x0_given) GS_TRY(adjoint_of_residual<double>(P, P->d, st));
     // D.vr holds r, D.vs = T^H r, scal[S_TMP] = ||T^H r||^2
     GS_TRY(cgls_pass<double>(P, P->d, thr2, o.maxit, check, false, st, &total, &stop));
-    k_addto<double><<<grid_for(nc), 256, 0, st>>>(x64, P->d.vx, nc);
+    GS_LAUNCH("solve_addto", st, k_addto<double><<<grid_for(nc), 256, 0, st>>>(x64, P->d.vx, nc));
     GS_TRY(residual64(P, st));
     GS_TRY(adjoint_of_residual<double>(P, P->d, st));
     ns2 = read_scal(P, S_TMP, st, &err);
@@ -319,7 +325,7 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
         GS_TRY(adjoint_of_residual<double>(P, P->d, st));
         ns2 = read_scal(P, S_TMP, st, &err);
         if (err != GS_OK) return err;
-        k_to32<<<grid_for(nc), 256, 0, st>>>(P->f.vs, P->d.vs, nc);
+        GS_LAUNCH("solve_to32", st, k_to32<<<grid_for(nc), 256, 0, st>>>(P->f.vs, P->d.vs, nc));
         GS_CUDA(cudaGetLastError());
         return norm2_into<float>(P, P->f.vs, nc, S_TMP, nullptr, st);
       }
@@ -335,7 +341,7 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
       GS_TRY(cgls_pass<float>(P, P->f, thr_pass, o.maxit - total, check, true, st, &it, &stop));
       total += it;
       inf.outer = outer + 1;
-      k_addto<float><<<grid_for(nc), 256, 0, st>>>(x64, P->f.vx, nc);
+      GS_LAUNCH("solve_addto", st, k_addto<float><<<grid_for(nc), 256, 0, st>>>(x64, P->f.vx, nc));
       GS_TRY(residual64(P, st));
       GS_TRY(check_value());
       if (stop == F_BREAK) break;
