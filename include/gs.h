@@ -60,8 +60,8 @@ typedef enum {
 
 /* Plan options; pass NULL for the defaults in brackets. */
 typedef struct {
-  int kb_m_hi;  /* Kaiser-Bessel half-width (taps per dim = 2m) for GS_FP64 applies [8] */
-  int kb_m_lo;  /* Kaiser-Bessel half-width for GS_FP32 applies [4] */
+  int kb_m_hi;  /* Kaiser-Bessel half-width m in 2..8 (taps per dim 2m) for GS_FP64 applies [8] */
+  int kb_m_lo;  /* Kaiser-Bessel half-width m in 2..8 for GS_FP32 applies [4] */
   int sigma;    /* oversampling factor of the NFFT grid, 2 or 4 [2] */
   int direct;   /* 1: evaluate T entry by entry (O(M N^d) per apply, small problems);
                    0: NFFT path; -1: choose (direct when M * N^d <= 2^20) [-1] */

@@ -73,8 +73,14 @@ void prof_end(cudaStream_t st) {
   if (!p.recs.empty()) cudaEventRecord(p.recs.back().b, st);
 }
 
+template <typename R>
+static void free_graphs(PrecData<R>& D) {
+  for (int i = 0; i < 2; ++i)
+    if (D.cg_exec[i]) cudaGraphExecDestroy(D.cg_exec[i]);
+}
+
 static void free_prec_f(PrecData<float>& D) {
-  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
+  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -87,10 +93,13 @@ static void free_prec_d(PrecData<double>& D) {
 }
 
 static void free_plan(Plan* P) {
-  void* ps[] = {P->perm, P->fl, P->xi_sorted, P->bin_start, P->work, P->work_start,
+  void* ps[] = {P->perm, P->fl, P->xi_sorted, P->bin_start, P->work, P->work_start, P->wcol, P->wcol_start,
                 P->red, P->scal, P->flag, P->y64, P->r64, P->x64};
   for (void* p : ps)
     if (p) cudaFree(p);
+  free_graphs(P->d);
+  free_graphs(P->f);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   free_prec_d(P->d);
   free_prec_f(P->f);
 }
@@ -127,8 +136,8 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
       }
   gs_opts o = {8, 4, 2, -1};
   if (opts) o = *opts;
-  if (o.kb_m_hi < 2 || o.kb_m_hi > 12 || o.kb_m_lo < 2 || o.kb_m_lo > 12 || (o.sigma != 2 && o.sigma != 4)) {
-    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..12), sigma = %d (2 or 4)", o.kb_m_hi, o.kb_m_lo,
+  if (o.kb_m_hi < 2 || o.kb_m_hi > 8 || o.kb_m_lo < 2 || o.kb_m_lo > 8 || (o.sigma != 2 && o.sigma != 4)) {
+    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..8), sigma = %d (2 or 4)", o.kb_m_hi, o.kb_m_lo,
               o.sigma);
     return GS_EINVAL;
   }
@@ -150,6 +159,11 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
   P->m_hi = o.kb_m_hi;
   P->m_lo = o.kb_m_lo;
   P->bandwidth = bandwidth;
+  if (dims == 2 && ((o.kb_m_hi != 4 && o.kb_m_hi != 6 && o.kb_m_hi != 8) ||
+                    (o.kb_m_lo != 4 && o.kb_m_lo != 6 && o.kb_m_lo != 8))) {
+    set_error("2D plans take Kaiser-Bessel half-widths 4, 6 or 8 (kb_m_hi = %d, kb_m_lo = %d)", o.kb_m_hi, o.kb_m_lo);
+    return GS_EINVAL;
+  }
   int mmax = o.kb_m_hi > o.kb_m_lo ? o.kb_m_hi : o.kb_m_lo;
   const int tile = (dims == 1) ? TILE1 : TILE2;
   const int64_t eff_tile = P->n < tile ? P->n : tile;
@@ -173,6 +187,7 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
     return GS_EUNSUPPORTED;
   }
   GS_CUDA(cudaGetDevice(&P->dev));
+  GS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   gs_status s = build_plan(P, xi, weights, (cudaStream_t)stream);
   if (s != GS_OK) {
     free_plan(P);

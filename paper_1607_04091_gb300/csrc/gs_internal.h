@@ -77,6 +77,7 @@ struct PrecData {
   double beta = 0;      // KB shape pi (2 - 1/sigma)
   // per-sample tables, sorted order
   R* frac = nullptr;    // [dims][M] fractional grid coordinate in [0, 1)
+  R* win = nullptr;     // float32 only: [M][dims][2m] window values phi(frac + m - 1 - a)
   C<R>* w = nullptr;    // [dims][M] interior factor (x factor carries sqrt(mu))
   C<R>* bf = nullptr;   // [dims][M][2b] boundary factors: left k=0..b-1 then right k=0..b-1
   R* deap = nullptr;    // [N] 1/psi(k_i) per coefficient index i (interior only)
@@ -95,6 +96,9 @@ struct PrecData {
   C<R>* vr = nullptr;  // M
   C<R>* vq = nullptr;  // M
   C<R>* vz = nullptr;  // ncoef (T^H q in the normal-equation recursion)
+  // captured CG pass (while-conditional graph), [0] CGLS form, [1] CGNR form
+  cudaGraphExec_t cg_exec[2] = {nullptr, nullptr};
+  bool cg_failed[2] = {false, false};
 };
 
 struct Plan {
@@ -112,6 +116,8 @@ struct Plan {
   int32_t* bin_start = nullptr;  // [nbins + 1] sample range of each bin
   int32_t* work = nullptr;       // [nwork][3] (bin, s0, s1)
   int32_t* work_start = nullptr; // [nbins + 1] work items of each bin
+  int32_t* wcol = nullptr;       // work items grouped by bin column (bx), then row
+  int32_t* wcol_start = nullptr; // [nbx + 1] offsets into wcol
   int nwork = 0;
   PrecData<double> d;
   PrecData<float> f;
@@ -122,7 +128,7 @@ struct Plan {
   double* y64 = nullptr;    // M, sorted-order data (complex128)
   double* r64 = nullptr;    // M, FP64 residual (complex128)
   double* x64 = nullptr;    // ncoef complex128 accumulator
-  cudaStream_t stream = 0;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
 };
 
 // implemented in tables.cu
@@ -145,6 +151,11 @@ template <typename R>
 inline gs_status apply_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st) {
   return P->direct ? direct_TH<R>(P, D, y, z, perm, st) : nfft_TH<R>(P, D, y, z, perm, st);
 }
+// per-sample 2D kernels (persample2d_f32.cu / persample2d_f64.cu)
+template <typename R>
+gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st);
+template <typename R>
+gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st);
 template <typename R>
 gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st);
 template <typename R>

@@ -17,53 +17,17 @@
 //   hbuf  [j][lx]      N x n: x-transform of every coefficient row j (2D)
 //   side  [2][2b][n]   forward: x-side grids along y; adjoint: both side grids
 //   part  per spread work item: padded tile, side segments, corner sums
+#include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "gs_internal.h"
+#include "device_common.cuh"
 
 namespace gs {
 
 namespace {
-
-template <typename R> __device__ inline C<R> mk(R a, R b);
-template <> __device__ inline float2 mk<float>(float a, float b) { return make_float2(a, b); }
-template <> __device__ inline double2 mk<double>(double a, double b) { return make_double2(a, b); }
-
-template <typename T> __device__ inline T cmul(T a, T b) {
-  T r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-template <typename T> __device__ inline T cmulc(T a, T b) {  // a * conj(b)
-  T r;
-  r.x = a.x * b.x + a.y * b.y;
-  r.y = a.y * b.x - a.x * b.y;
-  return r;
-}
-template <typename T> __device__ inline T cadd(T a, T b) {
-  a.x += b.x;
-  a.y += b.y;
-  return a;
-}
-template <typename T, typename R> __device__ inline T cscale(T a, R s) {
-  a.x *= s;
-  a.y *= s;
-  return a;
-}
-
-__device__ inline float kb_window(float d, int m, float beta) {
-  float s2 = (float)(m * m) - d * d;
-  if (s2 <= 0.0f) return beta * 0.318309886183790672f;
-  float s = sqrtf(s2);
-  return sinhf(beta * s) / (3.14159265358979323846f * s);
-}
-__device__ inline double kb_window(double d, int m, double beta) {
-  double s2 = (double)(m * m) - d * d;
-  if (s2 <= 0.0) return beta / M_PI;
-  double s = sqrt(s2);
-  return sinh(beta * s) / (M_PI * s);
-}
+using namespace dev;
 
 __device__ inline int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
 
@@ -208,15 +172,22 @@ __global__ void k_reduce1d(const int32_t* __restrict__ work_start, const C<R>* _
   grid[gx] = acc;
 }
 
-// boundary (or corner) channel sums over all work items
+// boundary (or corner) channel sums over all work items: one CTA per channel,
+// threads stride over the work items, fixed-order tree sum
 template <typename R>
 __global__ void k_reduce_chan(const C<R>* __restrict__ part, int64_t stride, int64_t off, int nch,
                               int nwork, C<R>* __restrict__ out) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nch) return;
+  __shared__ C<R> red[256];
+  const int c = blockIdx.x;
   C<R> acc = mk<R>(0, 0);
-  for (int wi = 0; wi < nwork; ++wi) acc = cadd(acc, part[wi * stride + off + c]);
-  out[c] = acc;
+  for (int wi = threadIdx.x; wi < nwork; wi += blockDim.x) acc = cadd(acc, part[wi * stride + off + c]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
 }
 
 // inverse FFT + crop + deapodise + boundary adjoint
@@ -301,163 +272,10 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
   }
 }
 
-// interpolation + factors + sides + corners, one thread per sorted sample
-template <typename R>
-__global__ void k_interp2d(const int32_t* __restrict__ fl, const R* __restrict__ frac,
-                           const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b,
-                           const C<R>* __restrict__ grid, const C<R>* __restrict__ hbuf,
-                           const C<R>* __restrict__ side, int n, int m, R beta,
-                           const C<R>* __restrict__ x, int N, int64_t M,
-                           const int32_t* __restrict__ perm, C<R>* __restrict__ y) {
-  __shared__ C<R> xc[GS_MAX_B * GS_MAX_B];
-  const int b2 = 2 * b;
-  for (int t = threadIdx.x; t < b2 * b2; t += blockDim.x) {
-    int kx = t % b2, ky = t / b2;
-    int i = (kx < b) ? kx : N - 1 - (kx - b);
-    int j = (ky < b) ? ky : N - 1 - (ky - b);
-    xc[t] = x[(int64_t)j * N + i];
-  }
-  __syncthreads();
-  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= M) return;
-  const int fx = fl[s], fy = fl[M + s];
-  const R tx = frac[s], ty = frac[M + s];
-  R wx[32], wy[32];
-  for (int a = 0; a < 2 * m; ++a) {
-    wx[a] = kb_window(tx + (R)(m - 1 - a), m, beta);
-    wy[a] = kb_window(ty + (R)(m - 1 - a), m, beta);
-  }
-  int ly[32];
-  for (int c = 0; c < 2 * m; ++c) ly[c] = ((fy - m + 1 + c) % n + n) % n;
-  C<R> vi = mk<R>(0, 0);
-  for (int a = 0; a < 2 * m; ++a) {
-    int lx = ((fx - m + 1 + a) % n + n) % n;
-    const C<R>* row = grid + (int64_t)lx * n;
-    C<R> acc = mk<R>(0, 0);
-    for (int c = 0; c < 2 * m; ++c) {
-      C<R> g = row[ly[c]];
-      acc.x += wy[c] * g.x;
-      acc.y += wy[c] * g.y;
-    }
-    vi.x += wx[a] * acc.x;
-    vi.y += wx[a] * acc.y;
-  }
-  const C<R> wxs = w[s], wys = w[M + s];
-  C<R> out = cmul(cmul(wxs, wys), vi);
-  if (b > 0) {
-    const C<R>* bx = bf + s * b2;
-    const C<R>* by = bf + (M + s) * b2;
-    C<R> sx = mk<R>(0, 0), sy = mk<R>(0, 0);
-    for (int k = 0; k < b2; ++k) {
-      // x-side k: 1D grid along y
-      const C<R>* g0 = side + (int64_t)k * n;
-      C<R> a0 = mk<R>(0, 0);
-      for (int c = 0; c < 2 * m; ++c) {
-        C<R> g = g0[ly[c]];
-        a0.x += wy[c] * g.x;
-        a0.y += wy[c] * g.y;
-      }
-      sx = cadd(sx, cmul(bx[k], a0));
-      // y-side k: row j = B(k) of the x transform, along x
-      int j = (k < b) ? k : N - 1 - (k - b);
-      const C<R>* g1 = hbuf + (int64_t)j * n;
-      C<R> a1 = mk<R>(0, 0);
-      for (int a = 0; a < 2 * m; ++a) {
-        int lx = ((fx - m + 1 + a) % n + n) % n;
-        C<R> g = g1[lx];
-        a1.x += wx[a] * g.x;
-        a1.y += wx[a] * g.y;
-      }
-      sy = cadd(sy, cmul(by[k], a1));
-    }
-    out = cadd(out, cmul(wys, sx));
-    out = cadd(out, cmul(wxs, sy));
-    C<R> cc = mk<R>(0, 0);
-    for (int ky = 0; ky < b2; ++ky) {
-      C<R> r = mk<R>(0, 0);
-      for (int kx = 0; kx < b2; ++kx) r = cadd(r, cmul(bx[kx], xc[ky * b2 + kx]));
-      cc = cadd(cc, cmul(by[ky], r));
-    }
-    out = cadd(out, cc);
-  }
-  y[perm ? perm[s] : s] = out;
-}
-
 // ---------------------------------------------------------------- 2D adjoint
 // Spread of one work item (tile (bx, by), samples s0..s1): per warp a private
 // padded tile P[(T+2m)^2] ([px][py]), x-side segments S0[2b][T+2m] (along y),
 // y-side segments S1[2b][T+2m] (along x), corner sums in registers.
-template <typename R>
-__global__ void k_spread2d(const int32_t* __restrict__ work, const int32_t* __restrict__ fl,
-                           const R* __restrict__ frac, const C<R>* __restrict__ w,
-                           const C<R>* __restrict__ bf, int b, const C<R>* __restrict__ u,
-                           const int32_t* __restrict__ perm, int64_t M, int nbx, int tile, int m,
-                           R beta, C<R>* __restrict__ part, int64_t stride) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int PW = tile + 2 * m;
-  const int b2 = 2 * b;
-  const int wsz = PW * PW + 2 * b2 * PW + b2 * b2;  // P | S0 | S1 | corners
-  const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  C<R>* my = reinterpret_cast<C<R>*>(smraw) + (int64_t)wid * wsz;
-  R* wins = reinterpret_cast<R*>(reinterpret_cast<C<R>*>(smraw) + (int64_t)nw * wsz) + wid * 64;
-  C<R>* P = my;
-  C<R>* S0 = my + PW * PW;
-  C<R>* S1 = S0 + b2 * PW;
-  C<R>* CC = S1 + b2 * PW;
-  for (int i = lane; i < wsz; i += 32) my[i] = mk<R>(0, 0);
-  __syncwarp();
-  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
-  const int ox = (bin % nbx) * tile, oy = (bin / nbx) * tile;
-  const int tw = 2 * m;
-  for (int s = s0 + wid; s < s1; s += nw) {
-    const C<R> us = u[perm ? perm[s] : s];
-    const int px = fl[s] - ox + 1, py = fl[M + s] - oy + 1;
-    const R tx = frac[s], ty = frac[M + s];
-    for (int q = lane; q < 2 * tw; q += 32)
-      wins[q] = (q < tw) ? kb_window(tx + (R)(m - 1 - q), m, beta) : kb_window(ty + (R)(m - 1 - (q - tw)), m, beta);
-    __syncwarp();
-    const C<R> wxs = w[s], wys = w[M + s];
-    const C<R> vi = cmulc(cmulc(us, wxs), wys);
-    for (int t = lane; t < tw * tw; t += 32) {
-      int a = t / tw, c = t - a * tw;
-      R wv = wins[a] * wins[tw + c];
-      C<R>& dst = P[(px + a) * PW + (py + c)];
-      dst.x += wv * vi.x;
-      dst.y += wv * vi.y;
-    }
-    if (b > 0) {
-      const C<R>* bx = bf + s * b2;
-      const C<R>* by = bf + (M + s) * b2;
-      for (int t = lane; t < b2 * tw; t += 32) {
-        int k = t / tw, c = t - k * tw;
-        C<R> v0 = cmulc(cmulc(us, bx[k]), wys);  // x-side k, along y
-        C<R>& d0 = S0[k * PW + py + c];
-        R w0 = wins[tw + c];
-        d0.x += w0 * v0.x;
-        d0.y += w0 * v0.y;
-        C<R> v1 = cmulc(cmulc(us, wxs), by[k]);  // y-side k, along x
-        C<R>& d1 = S1[k * PW + px + c];
-        R w1 = wins[c];
-        d1.x += w1 * v1.x;
-        d1.y += w1 * v1.y;
-      }
-      for (int ch = lane; ch < b2 * b2; ch += 32) {
-        int kx = ch % b2, ky = ch / b2;
-        CC[ch] = cadd(CC[ch], cmulc(cmulc(us, bx[kx]), by[ky]));
-      }
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-  C<R>* out = part + blockIdx.x * stride;
-  const C<R>* all = reinterpret_cast<C<R>*>(smraw);
-  for (int i = threadIdx.x; i < wsz; i += blockDim.x) {
-    C<R> acc = mk<R>(0, 0);
-    for (int q = 0; q < nw; ++q) acc = cadd(acc, all[(int64_t)q * wsz + i]);
-    out[i] = acc;
-  }
-}
-
 __device__ inline int neighbours(int bx, int nbx, int* cand) {
   int nc = 0;
   for (int dx = -1; dx <= 1; ++dx) {
@@ -492,30 +310,40 @@ __global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<
   grid[(int64_t)gx * n + gy] = acc;
 }
 
-// side grids: which = 0 -> x-side k along y (segments S0, bins grouped by row),
-// which = 1 -> y-side k along x (segments S1, bins grouped by column)
+// side grids: which = 0 -> x-side k along y (segments S0; the work items of
+// the neighbouring bin rows are contiguous), which = 1 -> y-side k along x
+// (segments S1; work items of the neighbouring bin columns from the column
+// list).  One CTA per (tile of output points, k, which); threads split the
+// contributing work items, fixed-order tree sum.
 template <typename R>
-__global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const C<R>* __restrict__ part,
-                                int64_t stride, int nbx, int tile, int m, int n, int b2,
-                                C<R>* __restrict__ side) {
-  const int which = blockIdx.z;
-  const int k = blockIdx.y;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= n) return;
+__global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const int32_t* __restrict__ wcol,
+                                const int32_t* __restrict__ wcol_start, const C<R>* __restrict__ part,
+                                int64_t stride, int nbx, int tile, int m, int n, int b2, C<R>* __restrict__ side) {
+  __shared__ C<R> red[256];
+  const int which = blockIdx.z, k = blockIdx.y, gb = blockIdx.x;
+  const int pt = threadIdx.x % tile, wl = threadIdx.x / tile, nl = blockDim.x / tile;
+  const int g = gb * tile + pt;
   const int PW = tile + 2 * m;
   const int64_t off = (int64_t)PW * PW + (int64_t)which * b2 * PW + (int64_t)k * PW;
   int cn[3];
-  int nc = neighbours(g / tile, nbx, cn);
+  const int nc = neighbours(gb, nbx, cn);
   C<R> acc = mk<R>(0, 0);
   for (int ci = 0; ci < nc; ++ci) {
-    int q0 = ((g - cn[ci] * tile + m) % n + n) % n;
-    for (int o = 0; o < nbx; ++o) {
-      int nb = (which == 0) ? (cn[ci] * nbx + o) : (o * nbx + cn[ci]);
-      for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
-        for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + off + q]);
+    const int q0 = ((g - cn[ci] * tile + m) % n + n) % n;
+    const int r0 = (which == 0) ? work_start[cn[ci] * nbx] : wcol_start[cn[ci]];
+    const int r1 = (which == 0) ? work_start[(cn[ci] + 1) * nbx] : wcol_start[cn[ci] + 1];
+    for (int r = r0 + wl; r < r1; r += nl) {
+      const int wi = (which == 0) ? r : wcol[r];
+      for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + off + q]);
     }
   }
-  side[((int64_t)which * b2 + k) * n + g] = acc;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (wl == 0) {
+    C<R> t = mk<R>(0, 0);
+    for (int l = 0; l < nl; ++l) t = cadd(t, red[l * tile + pt]);
+    side[((int64_t)which * b2 + k) * n + g] = t;
+  }
 }
 
 // adjoint pass 2: inverse y-transform of grid columns -> hbuf[j][lx] (interior j),
@@ -616,7 +444,7 @@ gs_status set_smem(const void* fn, size_t bytes) {
   return GS_OK;
 }
 
-template <typename R> constexpr int pass_cols() { return sizeof(R) == 4 ? 8 : 4; }
+template <typename R> constexpr int pass_cols() { return 2; }
 
 }  // namespace
 
@@ -640,7 +468,7 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
               k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
                                                              x, N, M, perm, y));
   } else {
-    const int rows = 2;
+    const int rows = 1;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
@@ -654,9 +482,8 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
               k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
                                                                                 cols, D.tw, D.grid, D.side));
-    GS_LAUNCH(pname<R>("interp2d<f32>", "interp2d<f64>"), st,
-              k_interp2d<R><<<(M + 127) / 128, 128, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, D.hbuf, D.side, n,
-                                                             D.m, beta, x, N, M, perm, y));
+    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st);
+    if (si != GS_OK) return si;
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -683,34 +510,29 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
                                                              n, D.grid));
     if (b2 > 0)
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
-                k_reduce_chan<R><<<1, 32, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
+                k_reduce_chan<R><<<b2, 256, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
     size_t shf = (size_t)n * sizeof(C<R>);
     gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
               k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
   } else {
-    const int warps = 4;
     const int PW = tile + 2 * m;
-    const int wsz = PW * PW + 2 * b2 * PW + b2 * b2;
-    size_t sh = (size_t)warps * wsz * sizeof(C<R>) + (size_t)warps * 64 * sizeof(R);
-    gs_status s = set_smem<R>((const void*)k_spread2d<R>, sh);
+    const int wsz = PW * PW + 2 * b2 * PW;
+    gs_status s = launch_spread2d<R>(P, D, y, perm, D.part, st);
     if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("spread2d<f32>", "spread2d<f64>"), st,
-              k_spread2d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, M,
-                                                              P->nbx, tile, m, beta, D.part, D.part_stride));
     dim3 rg(P->nbx, P->nby), rb(tile, tile);
     GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
               k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
                                                     D.grid));
     if (b2 > 0) {
-      dim3 sg((n + 127) / 128, b2, 2);
+      dim3 sg(P->nbx, b2, 2);
       GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
-                k_reduce2d_side<R><<<sg, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
-                                                        b2, D.side));
+                k_reduce2d_side<R><<<sg, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, D.part,
+                                                        D.part_stride, P->nbx, tile, m, n, b2, D.side));
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
-                k_reduce_chan<R><<<(b2 * b2 + 63) / 64, 64, 0, st>>>(D.part, D.part_stride, wsz - b2 * b2,
-                                                                      b2 * b2, P->nwork, D.corner));
+                k_reduce_chan<R><<<b2 * b2, 256, 0, st>>>(D.part, D.part_stride, wsz, b2 * b2, P->nwork,
+                                                           D.corner));
     }
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
@@ -719,7 +541,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
               k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
                                                                               cols, D.tw, D.hbuf, z));
-    const int rows = 2;
+    const int rows = 1;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;

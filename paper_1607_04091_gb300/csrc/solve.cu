@@ -21,7 +21,7 @@ namespace gs {
 namespace {
 
 constexpr int RED_BLOCKS = 512;
-enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP };
+enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
 enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
 
 template <typename T> __device__ inline double sqn(T v) { return (double)v.x * v.x + (double)v.y * v.y; }
@@ -151,6 +151,7 @@ __global__ void k_init_pass(double* scal, int* flag, double thr2, double maxit) 
   scal[S_S0] = scal[S_TMP];
   scal[S_THR2] = thr2;
   scal[S_ITER] = 0.0;
+  scal[S_LOOP] = 0.0;
   scal[S_MAXIT] = maxit;
   flag[0] = (scal[S_TMP] <= thr2) ? F_CONV : F_RUN;
 }
@@ -168,53 +169,156 @@ gs_status norm2_into(Plan* P, const C<R>* v, int64_t n, int slot, const int* fla
   return GS_OK;
 }
 
-// One CG pass in precision R from d = 0, in either of two equivalent forms:
+// Condition of the while node of a captured CG pass: runs once per iteration,
+// unconditionally, and counts the iterations itself, so the loop ends after at
+// most scal[S_MAXIT] iterations whatever the stop flag holds.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* flag, double* scal) {
+  const double c = scal[S_LOOP] + 1.0;
+  scal[S_LOOP] = c;
+  cudaGraphSetConditional(h, (flag[0] == F_RUN && c < scal[S_MAXIT]) ? 1u : 0u);
+}
+// enter the loop only if the pass has work
+__global__ void k_loop_enter(cudaGraphConditionalHandle h, const int* flag, const double* scal) {
+  cudaGraphSetConditional(h, (flag[0] == F_RUN && scal[S_MAXIT] >= 1.0) ? 1u : 0u);
+}
+
+// One iteration of CG in either of two equivalent forms:
 //   CGLS (normal_eq = false): rhs r in D.vr, updated as r -= alpha q, s = T^H r;
 //   CGNR (normal_eq = true):  s updated as s -= alpha T^H q, never re-formed from r,
 //     so no large cancellation when r is nearly orthogonal to the range of T.
-// s0 must be in D.vs and ||s0||^2 in scal[S_TMP].  D.vx <- d.
+template <typename R>
+gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st) {
+  const int64_t nc = P->ncoef, M = P->M;
+  gs_status s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
+  if (s != GS_OK) return s;
+  GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
+  GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
+  if (normal_eq) {
+    GS_LAUNCH("cgls_axpy", st,
+              k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(D.vx, D.vp, nc, nullptr, nullptr, 0, P->scal, P->flag));
+    s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
+    if (s != GS_OK) return s;
+    GS_LAUNCH("cgls_axpy", st,
+              k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(nullptr, nullptr, 0, D.vs, D.vz, nc, P->scal, P->flag));
+  } else {
+    GS_LAUNCH("cgls_axpy", st,
+              k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal, P->flag));
+    s = apply_TH<R>(P, D, D.vr, D.vs, nullptr, st);
+    if (s != GS_OK) return s;
+  }
+  GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vs, nc, P->red, P->flag));
+  GS_LAUNCH("cgls_scalar", st, k_beta<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
+  GS_LAUNCH("cgls_axpy", st, k_update_p<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc, P->scal, P->flag));
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+// Capture a whole CG pass as one graph: [enter kernel] -> while(cond) { iteration; cond kernel }.
+template <typename R>
+gs_status build_cg_graph(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st, cudaGraphExec_t* out) {
+  cudaStream_t cs = P->cap_stream;
+  // eager applies into the scratch vectors q and z (recomputed before any use)
+  // so that kernel attributes are set outside capture
+  GS_CUDA(cudaStreamSynchronize(st));
+  {
+    gs_status s = apply_T<R>(P, D, D.vp, D.vq, nullptr, cs);
+    if (s == GS_OK) s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, cs);
+    if (s != GS_OK) return s;
+  }
+  GS_CUDA(cudaStreamSynchronize(cs));
+  cudaGraph_t g = nullptr;
+  GS_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+  }
+  // entry node
+  e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    k_loop_enter<<<1, 1, 0, cs>>>(h, P->flag, P->scal);
+    cudaGraph_t gg = nullptr;
+    e = cudaStreamEndCapture(cs, &gg);
+  }
+  cudaGraphNode_t enter = nullptr;
+  size_t nn = 1;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &enter, &nn);
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t wnode = nullptr;
+  if (e == cudaSuccess) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, &enter, nullptr, 1, &cp);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      gs_status s = cg_iteration<R>(P, D, normal_eq, cs);
+      k_loop_cond<<<1, 1, 0, cs>>>(h, P->flag, P->scal);
+      cudaGraph_t bb = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cs, &bb);
+      if (s != GS_OK) {
+        cudaGraphDestroy(g);
+        return s;
+      }
+      e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "capturing the CG pass graph");
+  return GS_OK;
+}
+
+// One CG pass in precision R from d = 0: D.vx <- d.  s0 = T^H r must already be
+// in D.vs, ||s0||^2 in scal[S_TMP] (and r in D.vr for the CGLS form).  The pass
+// runs as one captured graph when possible (no host polling, exact stop), else
+// as host-driven launches that check the stop flag every `check` iterations.
 template <typename R>
 gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, bool normal_eq, cudaStream_t st,
                     int* iters, int* stop) {
-  const int64_t nc = P->ncoef, M = P->M;
+  const int64_t nc = P->ncoef;
   GS_CUDA(cudaMemsetAsync(D.vx, 0, nc * sizeof(C<R>), st));
   GS_LAUNCH("solve_copy", st, k_copy<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc));
   GS_LAUNCH("solve_init_pass", st, k_init_pass<<<1, 1, 0, st>>>(P->scal, P->flag, thr2, (double)maxit));
   GS_CUDA(cudaGetLastError());
   int hflag = F_RUN;
   double hit = 0;
-  int done = 0;
-  while (true) {
+  const int gi = normal_eq ? 1 : 0;
+  bool graphed = false;
+  if (!prof_on() && !D.cg_failed[gi]) {
+    if (!D.cg_exec[gi]) {
+      if (build_cg_graph<R>(P, D, normal_eq, st, &D.cg_exec[gi]) != GS_OK) {
+        D.cg_failed[gi] = true;
+        D.cg_exec[gi] = nullptr;
+        cudaGetLastError();
+      }
+    }
+    if (D.cg_exec[gi]) {
+      GS_CUDA(cudaGraphLaunch(D.cg_exec[gi], st));
+      graphed = true;
+    }
+  }
+  if (graphed) {
     GS_CUDA(cudaMemcpyAsync(&hflag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaMemcpyAsync(&hit, P->scal + S_ITER, sizeof(double), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
-    if (hflag != F_RUN || done >= maxit) break;
-    for (int k = 0; k < check; ++k) {
-      gs_status s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
-      if (s != GS_OK) return s;
-      GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
-      GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
-      if (normal_eq) {
-        GS_LAUNCH("cgls_axpy", st,
-                  k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(D.vx, D.vp, nc, nullptr, nullptr, 0, P->scal,
-                                                               P->flag));
-        s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
+  } else {
+    int done = 0;
+    while (true) {
+      GS_CUDA(cudaMemcpyAsync(&hflag, P->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      GS_CUDA(cudaMemcpyAsync(&hit, P->scal + S_ITER, sizeof(double), cudaMemcpyDeviceToHost, st));
+      GS_CUDA(cudaStreamSynchronize(st));
+      if (hflag != F_RUN || done >= maxit) break;
+      for (int k = 0; k < check; ++k) {
+        gs_status s = cg_iteration<R>(P, D, normal_eq, st);
         if (s != GS_OK) return s;
-        GS_LAUNCH("cgls_axpy", st,
-                  k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(nullptr, nullptr, 0, D.vs, D.vz, nc, P->scal,
-                                                               P->flag));
-      } else {
-        GS_LAUNCH("cgls_axpy", st,
-                  k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal,
-                                                                   P->flag));
-        s = apply_TH<R>(P, D, D.vr, D.vs, nullptr, st);
-        if (s != GS_OK) return s;
+        ++done;
       }
-      GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vs, nc, P->red, P->flag));
-      GS_LAUNCH("cgls_scalar", st, k_beta<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
-      GS_LAUNCH("cgls_axpy", st, k_update_p<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc, P->scal, P->flag));
-      GS_CUDA(cudaGetLastError());
-      ++done;
     }
   }
   *iters = (int)hit;

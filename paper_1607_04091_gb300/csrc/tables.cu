@@ -12,6 +12,7 @@
 // the recursion v1(eta) = U v1(eta/2) + V v2(eta/2) of App. A.1, unrolled D
 // times from v1(0), evaluated innermost-first together with phi-hat at every
 // level.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -177,7 +178,8 @@ __global__ void k_gather_fl(const int32_t* __restrict__ flo, const int32_t* __re
 __global__ void k_tables(const double* __restrict__ xs, const double* __restrict__ ms, int64_t M,
                          int dims, int J, int p, int b, double mu1, double mu2, int64_t n,
                          double2* __restrict__ w64, double2* __restrict__ bf64, double* __restrict__ fr64,
-                         float2* __restrict__ w32, float2* __restrict__ bf32, float* __restrict__ fr32) {
+                         float2* __restrict__ w32, float2* __restrict__ bf32, float* __restrict__ fr32,
+                         int m32, double beta32, float* __restrict__ win32) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= M * dims) return;
   int d = (int)(g / M);
@@ -267,6 +269,14 @@ __global__ void k_tables(const double* __restrict__ xs, const double* __restrict
   float f32 = (float)fr;
   if (f32 >= 1.0f) f32 = 0.99999994f;
   fr32[d * M + s] = f32;
+  // float32 window values of the 2m taps, evaluated in float64 at the float64
+  // coordinate: phi(dist) = sinh(beta sqrt(m^2 - dist^2)) / (pi sqrt(m^2 - dist^2))
+  for (int a = 0; a < 2 * m32; ++a) {
+    double dist = fr + (double)(m32 - 1 - a);
+    double s2 = (double)(m32 * m32) - dist * dist;
+    double v = (s2 <= 0.0) ? beta32 / M_PI : sinh(beta32 * sqrt(s2)) / (M_PI * sqrt(s2));
+    win32[((int64_t)s * dims + d) * (2 * m32) + a] = (float)v;
+  }
 }
 
 // deapodisation 1/psi(k), psi(k) = I0(m sqrt(beta^2 - (2 pi k/n)^2)), interior
@@ -320,6 +330,7 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
   const int64_t M = P->M, n = P->n, N = P->N;
   const int dims = P->dims, b = P->b, b2 = 2 * b;
   GS_TRY(dalloc(&D.frac, (size_t)dims * M));
+  if (sizeof(R) == 4) GS_TRY(dalloc(&D.win, (size_t)dims * M * 2 * m));
   GS_TRY(dalloc(&D.w, (size_t)dims * M));
   GS_TRY(dalloc(&D.bf, (size_t)dims * M * (b2 > 0 ? b2 : 1)));
   GS_TRY(dalloc(&D.deap, (size_t)N));
@@ -462,19 +473,33 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
     GS_CUDA(cudaMemcpyAsync(P->work, work.data(), work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   GS_CUDA(cudaMemcpyAsync(P->work_start, wstart.data(), wstart.size() * sizeof(int32_t),
                           cudaMemcpyHostToDevice, st));
+  // the same work items grouped by bin column (for reductions along x)
+  std::vector<int32_t> wcol, wcs(P->nbx + 1);
+  for (int bx = 0; bx < P->nbx; ++bx) {
+    wcs[bx] = (int32_t)wcol.size();
+    for (int by = 0; by < P->nby; ++by)
+      for (int32_t wi = wstart[by * P->nbx + bx]; wi < wstart[by * P->nbx + bx + 1]; ++wi) wcol.push_back(wi);
+  }
+  wcs[P->nbx] = (int32_t)wcol.size();
+  GS_TRY(dalloc(&P->wcol, wcol.size()));
+  GS_TRY(dalloc(&P->wcol_start, wcs.size()));
+  if (!wcol.empty())
+    GS_CUDA(cudaMemcpyAsync(P->wcol, wcol.data(), wcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemcpyAsync(P->wcol_start, wcs.data(), wcs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
 
   // per-precision tables and workspaces
   GS_TRY(alloc_prec(P, P->d, P->m_hi));
   GS_TRY(alloc_prec(P, P->f, P->m_lo));
   int64_t tot = M * dims;
   k_tables<<<(tot + 127) / 128, 128, 0, st>>>(P->xi_sorted, ms, M, dims, P->J, P->p, P->b, K.mu1, K.mu2,
-                                             P->n, P->d.w, P->d.bf, P->d.frac, P->f.w, P->f.bf, P->f.frac);
+                                             P->n, P->d.w, P->d.bf, P->d.frac, P->f.w, P->f.bf, P->f.frac,
+                                             P->f.m, P->f.beta, P->f.win);
   k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->d.m, P->d.beta, P->d.deap, nullptr, 0);
   k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->f.m, P->f.beta, nullptr, P->f.deap, 1);
   k_twiddle<<<(P->n / 2 + 255) / 256, 256, 0, st>>>(P->n, P->d.tw, P->f.tw);
   GS_CUDA(cudaGetLastError());
 
-  GS_TRY(dalloc(&P->red, 8192));
+  GS_TRY(dalloc(&P->red, (size_t)std::max(8192, P->nwork + 1024)));
   GS_TRY(dalloc(&P->scal, 64));
   GS_TRY(dalloc(&P->flag, 16));
   GS_TRY(dalloc(&P->y64, (size_t)2 * M));
