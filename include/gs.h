@@ -100,6 +100,18 @@ gs_status gs_apply_T(gs_plan plan, int precision, const void* x, void* y, void* 
 /* x = T^H y (Sec. 3.2 adjoint NDFT; App. C adjoint).  Buffers as gs_apply_T. */
 gs_status gs_apply_TH(gs_plan plan, int precision, const void* y, void* x, void* stream);
 
+/* x = T^H y like gs_apply_TH, for callers that must not allocate device memory
+ * while they run (code recording a CUDA graph, runtimes with a fixed memory
+ * arena).  The paper has no counterpart; it is a deployment variant.  The spread
+ * scratch lives in a fixed 8 MiB device array reserved by the library on every
+ * device that loads it; the call allocates nothing.  NFFT-path plans only
+ * (GS_EUNSUPPORTED for direct mode); GS_EINVAL when the plan's scratch exceeds
+ * 8 MiB (nwork * part_stride complex values).  All calls share the array, so
+ * calls whose GPU work overlaps race: order them on one stream.  The first call
+ * on a device looks up the array address (cudaGetSymbolAddress); make it before
+ * any stream capture.  Buffers as gs_apply_TH. */
+gs_status gs_apply_TH_noalloc(gs_plan plan, int precision, const void* y, void* x, void* stream);
+
 /* Solver settings for gs_solve. */
 typedef enum {
   GS_SOLVE_FP64 = 0,  /* textbook CGLS with GS_FP64 applies throughout */

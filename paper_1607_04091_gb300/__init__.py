@@ -40,6 +40,7 @@ class GsError(RuntimeError):
 
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
+           "gs_apply_TH_noalloc",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
            "gs_last_error_detail"]
 
@@ -63,6 +64,7 @@ def load(path: str = LIB):
                                   ctypes.POINTER(i64)]
     lib.gs_apply_T.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.gs_apply_TH.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    lib.gs_apply_TH_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.gs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo), vp]
     lib.gs_boundary_constants.argtypes = [ctypes.c_int] + [dp] * 7
     lib.gs_boundary_constants.restype = ctypes.c_int
@@ -73,7 +75,8 @@ def load(path: str = LIB):
     lib.gs_strerror.argtypes = [ctypes.c_int]
     lib.gs_strerror.restype = ctypes.c_char_p
     lib.gs_last_error_detail.restype = ctypes.c_char_p
-    for f in ["gs_plan_1d", "gs_plan_2d", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH", "gs_solve"]:
+    for f in ["gs_plan_1d", "gs_plan_2d", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH", "gs_apply_TH_noalloc",
+              "gs_solve"]:
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -186,6 +189,15 @@ def gs_apply_TH(plan, precision: int, y, x, stream=None):
     _, M, _, nc = gs_plan_sizes(plan)
     dt = _ctype(precision)
     _check(load().gs_apply_TH(plan, precision, _dev(y, dt, M), _dev(x, dt, nc), _stream(stream)), "gs_apply_TH")
+    return x
+
+
+def gs_apply_TH_noalloc(plan, precision: int, y, x, stream=None):
+    """x = T^H y through the entry point that allocates nothing (fixed static scratch)."""
+    _, M, _, nc = gs_plan_sizes(plan)
+    dt = _ctype(precision)
+    _check(load().gs_apply_TH_noalloc(plan, precision, _dev(y, dt, M), _dev(x, dt, nc), _stream(stream)),
+           "gs_apply_TH_noalloc")
     return x
 
 

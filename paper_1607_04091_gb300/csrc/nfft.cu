@@ -554,6 +554,74 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
   return GS_OK;
 }
 
+// The adjoint of nfft_TH with the spread's per-work-item partial sums in a
+// caller-given buffer `part` (nwork x part_stride) instead of the plan's.
+template <typename R>
+gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
+                          cudaStream_t st) {
+  const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
+  const int64_t M = P->M;
+  const R beta = (R)D.beta;
+  const int m = D.m, tile = P->tile;
+  if (P->nwork == 0) {
+    GS_CUDA(cudaMemsetAsync(z, 0, P->ncoef * sizeof(C<R>), st));
+    return GS_OK;
+  }
+  if (P->dims == 1) {
+    const int warps = 4;
+    size_t sh = (size_t)warps * (tile + 2 * m + b2) * sizeof(C<R>);
+    GS_LAUNCH(pname<R>("spread1d<f32>", "spread1d<f64>"), st,
+              k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile,
+                                                              m, beta, part, D.part_stride));
+    GS_LAUNCH(pname<R>("reduce1d<f32>", "reduce1d<f64>"), st,
+              k_reduce1d<R><<<(n + 127) / 128, 128, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m,
+                                                             n, D.grid));
+    if (b2 > 0)
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
+                k_reduce_chan<R><<<b2, 256, 0, st>>>(part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
+    size_t shf = (size_t)n * sizeof(C<R>);
+    gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
+    if (s != GS_OK) return s;
+    GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
+              k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+  } else {
+    const int PW = tile + 2 * m;
+    const int wsz = PW * PW + 2 * b2 * PW;
+    gs_status s = launch_spread2d<R>(P, D, y, perm, part, st);
+    if (s != GS_OK) return s;
+    dim3 rg(P->nbx, P->nby), rb(tile, tile);
+    GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+              k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m, n,
+                                                    D.grid));
+    if (b2 > 0) {
+      dim3 sg(P->nbx, b2, 2);
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
+                k_reduce2d_side<R><<<sg, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, part,
+                                                        D.part_stride, P->nbx, tile, m, n, b2, D.side));
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
+                k_reduce_chan<R><<<b2 * b2, 256, 0, st>>>(part, D.part_stride, wsz, b2 * b2, P->nwork,
+                                                           D.corner));
+    }
+    const int cols = pass_cols<R>();
+    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
+    s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
+    if (s != GS_OK) return s;
+    GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
+              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
+                                                                              cols, D.tw, D.hbuf, z));
+    const int rows = 1;
+    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+    s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
+    if (s != GS_OK) return s;
+    GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+                                                                         D.corner, D.deap, N, n, logn, b, rows,
+                                                                         D.tw, z));
+  }
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
 template <typename R>
 gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st) {
   GS_LAUNCH(pname<R>("gather<f32>", "gather<f64>"), st, k_gather<R><<<(P->M + 255) / 256, 256, 0, st>>>(y_user, P->perm, P->M, y_sorted));
@@ -572,6 +640,10 @@ template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, doub
 template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
 template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,
                                    cudaStream_t);
+template gs_status nfft_TH_scratch<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, float2*,
+                                          cudaStream_t);
+template gs_status nfft_TH_scratch<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,
+                                           double2*, cudaStream_t);
 template gs_status gather_sorted<float>(Plan*, const float2*, float2*, cudaStream_t);
 template gs_status gather_sorted<double>(Plan*, const double2*, double2*, cudaStream_t);
 template gs_status scatter_user<float>(Plan*, const float2*, float2*, cudaStream_t);
