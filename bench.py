@@ -110,14 +110,19 @@ def workload():
 
 # bytes one launch of each kernel must move (tables it streams + its input and
 # output vectors; the oversampled grids are method-internal and not counted)
-def kernel_bytes(name, M, N, b):
+def kernel_bytes(name, M, N, b, m_lo=4, m_hi=8):
+    """Bytes per launch: per sample the grid cell (2 int32), the float32 window
+    table (2 x 2m float) or, in float64, the fractional coordinates (2 double),
+    the interior factors (2 complex) and the boundary factors (2 x 2b complex),
+    plus the sample value read or written; the corner coefficients once."""
     f32 = "<f32>" in name
-    sc, sr = (8, 4) if f32 else (16, 8)
-    per_sample = 2 * 4 + 2 * sr + 2 * sc + 2 * (2 * b) * sc  # fl, frac, w, boundary factors
+    sc = 8 if f32 else 16
+    coord = 2 * (2 * m_lo) * 4 if f32 else 2 * 8
+    per_sample = 2 * 4 + coord + 2 * sc + 2 * (2 * b) * sc
     if name.startswith("interp2d"):
-        return M * (per_sample + sc) + (2 * b) ** 2 * sc  # + y out, + corner coefficients
+        return M * (per_sample + sc) + (2 * b) ** 2 * sc
     if name.startswith("spread2d"):
-        return M * (per_sample + sc + 4)  # + y in (gathered through perm)
+        return M * (per_sample + sc)
     return None
 
 
@@ -151,12 +156,16 @@ def main():
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--probe-apply", type=int, default=0,
+                    help="only run this many float32 T^H and T applies on the workload (for profilers)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank)
+    if args.probe_apply:
+        return probe_apply(args.probe_apply)
 
     import torch
     import paper_1607_04091_gb300 as gs
@@ -257,9 +266,9 @@ def main():
         try:
             tr = json.load(open(tfile))
             ent = tr.get(name)
-            src = open(os.path.join(ROOT, "paper_1607_04091_gb300", "csrc", "nfft.cu"), "rb").read()
             import hashlib
-            if ent and ent.get("nfft_cu_sha1") == hashlib.sha1(src).hexdigest():
+            src = open(os.path.join(ROOT, "paper_1607_04091_gb300", "csrc", ent["source"]), "rb").read() if ent else b""
+            if ent and ent.get("source_sha1") == hashlib.sha1(src).hexdigest():
                 traffic = ent["dram_bytes_per_launch"]
         except Exception:
             traffic = None
@@ -311,6 +320,29 @@ def main():
         "fp64_cgls": fp64, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def probe_apply(reps):
+    """float32 T^H then T on the workload's plan, `reps` times; CUDA-event timings."""
+    import torch
+    import paper_1607_04091_gb300 as gs
+
+    xi, mu, _, _ = workload()
+    plan = gs.Plan.plan_2d(xi, P_VM, J, weights=mu)
+    g = np.random.default_rng(0)
+    y = torch.tensor(g.standard_normal(plan.M) + 1j * g.standard_normal(plan.M), dtype=torch.complex64, device="cuda")
+    x = torch.tensor(g.standard_normal(plan.ncoef) + 1j * g.standard_normal(plan.ncoef), dtype=torch.complex64,
+                     device="cuda")
+    z, q = torch.empty_like(x), torch.empty_like(y)
+    for r in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        gs.gs_apply_TH(plan.handle, gs.GS_FP32, y, z)
+        e[1].record()
+        gs.gs_apply_T(plan.handle, gs.GS_FP32, x, q)
+        e[2].record()
+        torch.cuda.synchronize()
+        log(f"apply {r}: T^H {e[0].elapsed_time(e[1]) * 1e3:.1f} us, T {e[1].elapsed_time(e[2]) * 1e3:.1f} us")
 
 
 def reference_arm(args, rank):

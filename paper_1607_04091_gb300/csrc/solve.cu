@@ -12,6 +12,7 @@
 // adjoint (float32, exact enough because r is small) gives the stop test.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "gs_internal.h"
@@ -277,7 +278,9 @@ gs_status build_cg_graph(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t s
 // One CG pass in precision R from d = 0: D.vx <- d.  s0 = T^H r must already be
 // in D.vs, ||s0||^2 in scal[S_TMP] (and r in D.vr for the CGLS form).  The pass
 // runs as one captured graph when possible (no host polling, exact stop), else
-// as host-driven launches that check the stop flag every `check` iterations.
+// as host-driven launches that check the stop flag every `check` iterations
+// (also when tracing is on or the environment sets GS_NO_GRAPHS, e.g. for
+// profilers that replay kernels one by one).
 template <typename R>
 gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, bool normal_eq, cudaStream_t st,
                     int* iters, int* stop) {
@@ -290,7 +293,8 @@ gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, 
   double hit = 0;
   const int gi = normal_eq ? 1 : 0;
   bool graphed = false;
-  if (!prof_on() && !D.cg_failed[gi]) {
+  static const bool no_graphs = std::getenv("GS_NO_GRAPHS") != nullptr;
+  if (!prof_on() && !no_graphs && !D.cg_failed[gi]) {
     if (!D.cg_exec[gi]) {
       if (build_cg_graph<R>(P, D, normal_eq, st, &D.cg_exec[gi]) != GS_OK) {
         D.cg_failed[gi] = true;
