@@ -150,6 +150,18 @@ typedef struct {
 gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* opts,
                    gs_solve_info* info, void* stream);
 
+/* B independent least-squares solves (one plan each, plans distinct) with the
+ * options of gs_solve.  Each GS_SOLVE_MIXED solve with tol >= 1e-7 and no start
+ * guess runs as one CUDA graph (nested while-conditional nodes: refinement
+ * passes around CG iterations, float64 residual and stop test on the device);
+ * the B graphs are launched round-robin on 16 library-owned streams ordered
+ * after `stream`, with no host synchronisation until all have finished.  Other
+ * option combinations fall back to gs_solve per problem.  y[i], x[i] as in
+ * gs_solve; infos (host, B entries) may be NULL.  Returns the first non-OK
+ * status of any problem (GS_ENOTCONV included). */
+gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
+                         const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
+
 /* Host-only (no CUDA call): the plan-time constants for p vanishing moments, so
  * they can be checked without a GPU.  h: 2p filter taps h_k, k = -p+1..p, with
  * sum 1 (App. A).  For p >= 2 also the edge matrices of App. A.1, row-major:

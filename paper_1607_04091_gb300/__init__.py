@@ -40,7 +40,7 @@ class GsError(RuntimeError):
 
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
-           "gs_apply_TH_noalloc",
+           "gs_apply_TH_noalloc", "gs_solve_batch",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
            "gs_last_error_detail"]
 
@@ -66,6 +66,9 @@ def load(path: str = LIB):
     lib.gs_apply_TH.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.gs_apply_TH_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     lib.gs_solve.argtypes = [vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo), vp]
+    lib.gs_solve_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo), vp]
+    lib.gs_solve_batch.restype = ctypes.c_int
     lib.gs_boundary_constants.argtypes = [ctypes.c_int] + [dp] * 7
     lib.gs_boundary_constants.restype = ctypes.c_int
     lib.gs_profile.argtypes = [ctypes.c_int]
@@ -214,6 +217,27 @@ def gs_solve(plan, y, x, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED, x0_given=Fal
         _check(st, "gs_solve")
     return {"iterations": info.iterations, "outer": info.outer, "rel_normres": info.rel_normres,
             "rel_res": info.rel_res, "status": info.status}
+
+
+def gs_solve_batch(plans, ys, xs, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED, max_outer=8, inner_rtol=0.0,
+                   stream=None):
+    """Solve B problems (plans[i], ys[i] -> xs[i], complex128 CUDA tensors); list of info dicts."""
+    import torch
+    B = len(plans)
+    hs = (ctypes.c_void_p * B)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    for p, y, x in zip(plans, ys, xs):
+        _, M, _, nc = gs_plan_sizes(p)
+        _dev(y, torch.complex128, M)
+        _dev(x, torch.complex128, nc)
+    yp = (ctypes.c_void_p * B)(*[y.data_ptr() for y in ys])
+    xp = (ctypes.c_void_p * B)(*[x.data_ptr() for x in xs])
+    o = GsSolveOpts(tol, maxit, mode, 0, max_outer, inner_rtol)
+    infos = (GsSolveInfo * B)()
+    st = load().gs_solve_batch(hs, B, yp, xp, ctypes.byref(o), infos, _stream(stream))
+    if st not in (GS_OK, GS_ENOTCONV):
+        _check(st, "gs_solve_batch")
+    return [{"iterations": i.iterations, "outer": i.outer, "rel_normres": i.rel_normres, "rel_res": i.rel_res,
+             "status": i.status} for i in infos]
 
 
 class Plan:

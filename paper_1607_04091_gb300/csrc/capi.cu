@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -99,6 +100,7 @@ static void free_plan(Plan* P) {
     if (p) cudaFree(p);
   free_graphs(P->d);
   free_graphs(P->f);
+  if (P->solve_exec) cudaGraphExecDestroy(P->solve_exec);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   free_prec_d(P->d);
   free_prec_f(P->f);
@@ -353,6 +355,41 @@ gs_status gs_profile_report(char* buf, int64_t len) {
   }
   memcpy(buf, out.c_str(), out.size() + 1);
   return GS_OK;
+}
+
+gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
+                         const gs_solve_opts* opts, gs_solve_info* infos, void* stream) {
+  if (!plans || !y || !x || B < 1) {
+    set_error("need plans, y, x non-NULL and B >= 1");
+    return GS_EINVAL;
+  }
+  gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
+  if (opts) o = *opts;
+  if (o.inner_rtol == 0.0) o.inner_rtol = 1e-4;
+  if (!(o.tol > 0.0) || o.maxit < 1 || (o.mode != GS_SOLVE_FP64 && o.mode != GS_SOLVE_MIXED) || o.max_outer < 1 ||
+      !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0)) {
+    set_error("bad solve options (tol > 0, maxit >= 1, mode 0/1, max_outer >= 1, 0 < inner_rtol < 1)");
+    return GS_EINVAL;
+  }
+  std::vector<Plan*> ps(B);
+  std::vector<const double*> ys(B);
+  std::vector<double*> xs(B);
+  for (int i = 0; i < B; ++i) {
+    if (!plans[i] || !y[i] || !x[i]) {
+      set_error("plans[%d], y[%d] and x[%d] must be non-NULL", i, i, i);
+      return GS_EINVAL;
+    }
+    ps[i] = &plans[i]->P;
+    ys[i] = (const double*)y[i];
+    xs[i] = (double*)x[i];
+  }
+  std::vector<Plan*> sorted = ps;
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+    set_error("a plan appears twice in the batch (its workspaces would be shared)");
+    return GS_EINVAL;
+  }
+  return solve_batch(ps.data(), B, ys.data(), xs.data(), o, infos, (cudaStream_t)stream);
 }
 
 const char* gs_strerror(gs_status s) {

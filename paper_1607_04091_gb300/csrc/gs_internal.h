@@ -129,6 +129,8 @@ struct Plan {
   double* r64 = nullptr;    // M, FP64 residual (complex128)
   double* x64 = nullptr;    // ncoef complex128 accumulator
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  cudaGraphExec_t solve_exec = nullptr;  // whole mixed solve as one graph
+  bool solve_graph_failed = false;
 };
 
 // implemented in tables.cu
@@ -166,6 +168,8 @@ gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t
 // implemented in solve.cu
 gs_status solve(Plan* P, const double* y, double* x, const gs_solve_opts& o, gs_solve_info* info,
                 cudaStream_t st);
+gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
+                      gs_solve_info* infos, cudaStream_t st);
 
 inline int ilog2(int64_t n) {
   int l = 0;

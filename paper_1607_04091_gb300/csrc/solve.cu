@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "gs_internal.h"
@@ -23,6 +24,8 @@ namespace {
 
 constexpr int RED_BLOCKS = 512;
 enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
+// scalars of the device-side mixed solve (solve graph)
+enum { G_TOL2 = 20, G_MAXIT, G_MAXOUT, G_IRTOL2, G_HB2, G_HY2, G_THR2, G_NS2, G_OUTER, G_TOTAL, G_NR2, G_STOP };
 enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
 
 template <typename T> __device__ inline double sqn(T v) { return (double)v.x * v.x + (double)v.y * v.y; }
@@ -379,10 +382,227 @@ double read_scal(Plan* P, int slot, cudaStream_t st, gs_status* err) {
   return v;
 }
 
+// ---------------------------------------------------------------- device-side mixed solve
+// One CUDA graph per plan runs a whole GS_SOLVE_MIXED solve (float32 stop test):
+//   setup -> [outer enter] -> while(outer) { pass init -> [inner enter] ->
+//   while(inner) { CG iteration; inner cond } -> x += d, r = y - T x (float64),
+//   s = T^H r (float32) -> outer cond } -> final
+// Every condition kernel runs unconditionally once per loop body and counts the
+// loop itself, so the inner loop ends after at most maxit - total iterations and
+// the outer loop after at most max_outer passes, whatever the data.
+__global__ void k_set_params(double* scal, double tol2, double maxit, double maxout, double irtol2) {
+  scal[G_TOL2] = tol2;
+  scal[G_MAXIT] = maxit;
+  scal[G_MAXOUT] = maxout;
+  scal[G_IRTOL2] = irtol2;
+}
+__global__ void k_solve_setup(double* scal, int* flag) {
+  const double hb2 = scal[S_TMP];
+  scal[G_HB2] = hb2;
+  scal[G_NS2] = hb2;
+  scal[G_THR2] = scal[G_TOL2] * hb2;
+  scal[G_OUTER] = 0.0;
+  scal[G_TOTAL] = 0.0;
+  scal[G_STOP] = 0.0;
+  scal[S_ITER] = 0.0;
+  flag[0] = F_RUN;
+}
+__global__ void k_outer_enter(cudaGraphConditionalHandle h, const double* scal) {
+  const bool go = scal[G_HB2] > 0.0 && scal[G_NS2] > scal[G_THR2] && scal[G_MAXOUT] >= 1.0 &&
+                  scal[G_TOTAL] < scal[G_MAXIT];
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+__global__ void k_pass_init(double* scal, int* flag) {
+  const double ns2 = scal[S_TMP];
+  const double thr = fmax(0.25 * scal[G_THR2], scal[G_IRTOL2] * ns2);
+  scal[S_GAMMA] = ns2;
+  scal[S_S0] = ns2;
+  scal[S_THR2] = thr;
+  scal[S_ITER] = 0.0;
+  scal[S_LOOP] = 0.0;
+  scal[S_MAXIT] = scal[G_MAXIT] - scal[G_TOTAL];
+  flag[0] = (ns2 <= thr) ? F_CONV : F_RUN;
+}
+__global__ void k_outer_cond(cudaGraphConditionalHandle h, const int* flag, double* scal) {
+  const double outer = scal[G_OUTER] + 1.0;
+  scal[G_OUTER] = outer;
+  scal[G_TOTAL] += scal[S_ITER];
+  scal[G_NS2] = scal[S_TMP];
+  if (flag[0] == F_BREAK) scal[G_STOP] = (double)F_BREAK;
+  const bool go = flag[0] != F_BREAK && scal[G_NS2] > scal[G_THR2] && outer < scal[G_MAXOUT] &&
+                  scal[G_TOTAL] < scal[G_MAXIT];
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// capture the launches of `enq` into a child-graph node of `parent` after `dep`
+template <typename F>
+gs_status add_child(cudaGraph_t parent, cudaGraphNode_t* dep, cudaStream_t cs, F&& enq, cudaGraphNode_t* out) {
+  GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  gs_status s = enq(cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (s != GS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "capturing a solve-graph segment");
+  e = cudaGraphAddChildGraphNode(out, parent, dep, dep ? 1 : 0, g);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphAddChildGraphNode");
+  return GS_OK;
+}
+
+gs_status add_kernel(cudaGraph_t parent, cudaGraphNode_t* dep, void* fn, void** args, cudaGraphNode_t* out) {
+  cudaKernelNodeParams kp = {};
+  kp.func = fn;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = args;
+  GS_CUDA(cudaGraphAddKernelNode(out, parent, dep, dep ? 1 : 0, &kp));
+  return GS_OK;
+}
+
+gs_status add_while(cudaGraph_t parent, cudaGraphNode_t* dep, cudaGraphConditionalHandle h, cudaGraphNode_t* out,
+                    cudaGraph_t* body) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  GS_CUDA(cudaGraphAddNode(out, parent, dep, nullptr, dep ? 1 : 0, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return GS_OK;
+}
+
+gs_status build_solve_graph(Plan* P, cudaStream_t st, cudaGraphExec_t* out) {
+  cudaStream_t cs = P->cap_stream;
+  PrecData<float>& F = P->f;
+  const int64_t nc = P->ncoef, M = P->M;
+  // eager applies so that kernel attributes are set outside capture
+  GS_CUDA(cudaStreamSynchronize(st));
+  GS_TRY(apply_T<float>(P, F, F.vp, F.vq, nullptr, cs));
+  GS_TRY(apply_TH<float>(P, F, F.vq, F.vz, nullptr, cs));
+  GS_TRY(apply_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, cs));
+  GS_CUDA(cudaStreamSynchronize(cs));
+  cudaGraph_t G = nullptr;
+  GS_CUDA(cudaGraphCreate(&G, 0));
+  struct Guard {
+    cudaGraph_t g;
+    ~Guard() {
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{G};
+  cudaGraphConditionalHandle ho, hi;
+  GS_CUDA(cudaGraphConditionalHandleCreate(&ho, G, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t n_setup, n_oenter, n_outer, n_final;
+  GS_TRY(add_child(G, nullptr, cs, [&](cudaStream_t c) -> gs_status {
+    GS_TRY(norm2_into<double>(P, (const double2*)P->y64, M, G_HY2, nullptr, c));
+    GS_CUDA(cudaMemsetAsync(P->x64, 0, nc * sizeof(double2), c));
+    k_copy<double><<<grid_for(M), 256, 0, c>>>((double2*)P->r64, (const double2*)P->y64, M);
+    GS_TRY(adjoint_of_residual<float>(P, F, c));
+    k_solve_setup<<<1, 1, 0, c>>>(P->scal, P->flag);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  }, &n_setup));
+  void* a_oenter[] = {&ho, &P->scal};
+  GS_TRY(add_kernel(G, &n_setup, (void*)k_outer_enter, a_oenter, &n_oenter));
+  cudaGraph_t outer_body = nullptr;
+  GS_TRY(add_while(G, &n_oenter, ho, &n_outer, &outer_body));
+  GS_CUDA(cudaGraphConditionalHandleCreate(&hi, outer_body, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t n_pinit, n_ienter, n_inner, n_post, n_ocond;
+  GS_TRY(add_child(outer_body, nullptr, cs, [&](cudaStream_t c) -> gs_status {
+    k_pass_init<<<1, 1, 0, c>>>(P->scal, P->flag);
+    GS_CUDA(cudaMemsetAsync(F.vx, 0, nc * sizeof(float2), c));
+    k_copy<float><<<grid_for(nc), 256, 0, c>>>(F.vp, F.vs, nc);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  }, &n_pinit));
+  void* a_ienter[] = {&hi, &P->flag, &P->scal};
+  GS_TRY(add_kernel(outer_body, &n_pinit, (void*)k_loop_enter, a_ienter, &n_ienter));
+  cudaGraph_t inner_body = nullptr;
+  GS_TRY(add_while(outer_body, &n_ienter, hi, &n_inner, &inner_body));
+  {
+    GS_CUDA(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    gs_status sc = cg_iteration<float>(P, F, true, cs);
+    k_loop_cond<<<1, 1, 0, cs>>>(hi, P->flag, P->scal);
+    cudaGraph_t bb = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &bb);
+    if (sc != GS_OK) return sc;
+    if (e != cudaSuccess) return cuda_fail(e, "capturing the CG iteration");
+  }
+  GS_TRY(add_child(outer_body, &n_inner, cs, [&](cudaStream_t c) -> gs_status {
+    k_addto<float><<<grid_for(nc), 256, 0, c>>>((double2*)P->x64, F.vx, nc);
+    GS_TRY(residual64(P, c));
+    return adjoint_of_residual<float>(P, F, c);
+  }, &n_post));
+  void* a_ocond[] = {&ho, &P->flag, &P->scal};
+  GS_TRY(add_kernel(outer_body, &n_post, (void*)k_outer_cond, a_ocond, &n_ocond));
+  GS_TRY(add_child(G, &n_outer, cs, [&](cudaStream_t c) -> gs_status {
+    return norm2_into<double>(P, (const double2*)P->r64, M, G_NR2, nullptr, c);
+  }, &n_final));
+  GS_CUDA(cudaGraphInstantiate(out, G, 0));
+  return GS_OK;
+}
+
+// mixed solve through the cached solve graph; y_user and x_user as in gs_solve
+gs_status launch_solve_graph(Plan* P, const double* y_user, double* x_user, const gs_solve_opts& o,
+                             cudaStream_t st) {
+  if (!P->solve_exec) {
+    gs_status s = build_solve_graph(P, st, &P->solve_exec);
+    if (s != GS_OK) {
+      P->solve_exec = nullptr;
+      P->solve_graph_failed = true;
+      return s;
+    }
+  }
+  GS_TRY(gather_sorted<double>(P, (const double2*)y_user, (double2*)P->y64, st));
+  k_set_params<<<1, 1, 0, st>>>(P->scal, o.tol * o.tol, (double)o.maxit, (double)o.max_outer,
+                                o.inner_rtol * o.inner_rtol);
+  GS_CUDA(cudaGetLastError());
+  GS_CUDA(cudaGraphLaunch(P->solve_exec, st));
+  GS_CUDA(cudaMemcpyAsync(x_user, P->x64, P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  return GS_OK;
+}
+
+// info of a finished graph solve (host reads the plan's scalars)
+gs_status graph_solve_info(Plan* P, const gs_solve_opts& o, gs_solve_info* info) {
+  double sc[40];
+  GS_CUDA(cudaMemcpy(sc, P->scal, sizeof(sc), cudaMemcpyDeviceToHost));
+  gs_solve_info inf = {0, 0, 0.0, 0.0, GS_OK};
+  const double hb2 = sc[G_HB2], hy2 = sc[G_HY2];
+  inf.iterations = (int)sc[G_TOTAL];
+  inf.outer = (int)sc[G_OUTER];
+  inf.rel_normres = hb2 > 0 ? std::sqrt(sc[G_NS2] / hb2) : 0.0;
+  inf.rel_res = hy2 > 0 ? std::sqrt((hb2 > 0 ? sc[G_NR2] : hy2) / hy2) : 0.0;
+  gs_status rc = GS_OK;
+  if (sc[G_STOP] == (double)F_BREAK) rc = GS_EBREAKDOWN;
+  else if (hb2 > 0 && sc[G_NS2] > sc[G_THR2]) rc = GS_ENOTCONV;
+  inf.status = rc;
+  if (info) *info = inf;
+  if (rc != GS_OK) set_error("solve stopped: relative normal-equation residual %.3e after %d iterations",
+                             inf.rel_normres, inf.iterations);
+  return rc;
+}
+
+bool graph_solve_ok(Plan* P, const gs_solve_opts& o) {
+  static const bool no_graphs = std::getenv("GS_NO_GRAPHS") != nullptr;
+  return o.mode == GS_SOLVE_MIXED && !o.x0_given && o.tol >= 1e-7 && !prof_on() && !no_graphs &&
+         !P->solve_graph_failed;
+}
+
 }  // namespace
 
 gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_opts& o, gs_solve_info* info,
                 cudaStream_t st) {
+  if (graph_solve_ok(P, o)) {
+    gs_status s = launch_solve_graph(P, y_user, x_user, o, st);
+    if (s == GS_OK) {
+      GS_CUDA(cudaStreamSynchronize(st));
+      return graph_solve_info(P, o, info);
+    }
+    if (!P->solve_graph_failed) return s;
+    cudaGetLastError();  // graph could not be built: fall through to host-driven passes
+  }
   const int64_t nc = P->ncoef, M = P->M;
   double2* y64 = (double2*)P->y64;
   double2* x64 = (double2*)P->x64;
@@ -470,6 +690,84 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
   if (rc != GS_OK) set_error("solve stopped: relative normal-equation residual %.3e after %d iterations",
                              inf.rel_normres, total);
   return rc;
+}
+
+}  // namespace gs
+
+// ---------------------------------------------------------------- batched solves
+namespace gs {
+namespace {
+constexpr int POOL = 16;
+struct StreamPool {
+  int dev = -1;
+  cudaStream_t s[POOL] = {};
+  cudaEvent_t done[POOL] = {};
+  cudaEvent_t start = nullptr;
+};
+StreamPool g_pools[64];
+std::mutex g_pool_mu;
+
+gs_status get_pool(StreamPool** out) {
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d unsupported", dev);
+    return GS_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  StreamPool& p = g_pools[dev];
+  if (p.dev < 0) {
+    for (int i = 0; i < POOL; ++i) {
+      GS_CUDA(cudaStreamCreateWithFlags(&p.s[i], cudaStreamNonBlocking));
+      GS_CUDA(cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming));
+    }
+    GS_CUDA(cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming));
+    p.dev = dev;
+  }
+  *out = &p;
+  return GS_OK;
+}
+}  // namespace
+
+gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
+                      gs_solve_info* infos, cudaStream_t st) {
+  StreamPool* pool = nullptr;
+  GS_TRY(get_pool(&pool));
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  GS_CUDA(cudaEventRecord(pool->start, st));
+  const int ns = B < POOL ? B : POOL;
+  for (int i = 0; i < ns; ++i) GS_CUDA(cudaStreamWaitEvent(pool->s[i], pool->start, 0));
+  std::vector<char> graphed(B, 0);
+  gs_status first = GS_OK;
+  for (int p = 0; p < B; ++p) {
+    cudaStream_t s = pool->s[p % ns];
+    if (graph_solve_ok(plans[p], o)) {
+      gs_status r = launch_solve_graph(plans[p], y[p], x[p], o, s);
+      if (r == GS_OK) {
+        graphed[p] = 1;
+        continue;
+      }
+      if (!plans[p]->solve_graph_failed) return r;
+      cudaGetLastError();
+    }
+    gs_solve_info inf;
+    gs_status r = solve(plans[p], y[p], x[p], o, &inf, s);  // host-driven fallback
+    if (infos) infos[p] = inf;
+    if (r != GS_OK && first == GS_OK) first = r;
+  }
+  for (int i = 0; i < ns; ++i) {
+    GS_CUDA(cudaEventRecord(pool->done[i], pool->s[i]));
+    GS_CUDA(cudaStreamWaitEvent(st, pool->done[i], 0));
+  }
+  GS_CUDA(cudaStreamSynchronize(st));
+  for (int p = 0; p < B; ++p) {
+    if (!graphed[p]) continue;
+    gs_solve_info inf;
+    gs_status r = graph_solve_info(plans[p], o, &inf);
+    if (infos) infos[p] = inf;
+    if (r != GS_OK && first == GS_OK) first = r;
+  }
+  return first;
 }
 
 }  // namespace gs

@@ -1,0 +1,88 @@
+"""Batched and graph-built solves (GPU) against the FP64 oracle.
+
+gs_solve in mixed mode with tol >= 1e-7 runs as one CUDA graph; gs_solve_batch
+runs many of them concurrently.  Each returned x is checked by the oracle: its
+FP64 normal-equation residual ||T^H (y - T x)|| / ||T^H y|| must meet the
+requested tolerance (with a 10% margin for the float32 adjoint in the device
+stop test), and the batch result must equal the one-at-a-time result.
+"""
+import numpy as np
+import pytest
+
+from oracle.operator import Basis1D, Operator1D, Operator2D
+from oracle.weights import voronoi_1d
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1607_04091_gb300 as gs  # noqa: E402
+
+
+def oracle_op(pr):
+    B = Basis1D(pr.p, pr.J)
+    if pr.dim == 1:
+        mu = voronoi_1d(pr.xi, pr.bandwidth)
+        return Operator1D(B, pr.xi, mu)
+    return Operator2D(B, pr.xi)
+
+
+def rel_normres(op, y, x):
+    return np.linalg.norm(op.adjoint(y - op.apply(x))) / np.linalg.norm(op.adjoint(y))
+
+
+def make_plan(pr):
+    if pr.dim == 1:
+        return gs.Plan.plan_1d(pr.xi, pr.p, pr.J, bandwidth=pr.bandwidth, direct=0)
+    return gs.Plan.plan_2d(pr.xi, pr.p, pr.J, direct=0)
+
+
+def small_batch(count=12):
+    return synth.batch_specs(count=count, seed=4004, J1=(6, 8), J2=(4, 5))
+
+
+def test_graph_solve_meets_tolerance_and_matches_host_path():
+    pr = small_batch(4)[2]  # a 2D problem
+    op = oracle_op(pr)
+    g = synth.rng(9)
+    y = op.apply(pr.x_true) + 1e-3 * synth.complex_gaussian(op.M, g)
+    plan = make_plan(pr)
+    x1, info1 = plan.solve(torch.tensor(y, device="cuda"), tol=1e-6)  # graph path
+    assert info1["status"] == gs.GS_OK
+    assert rel_normres(op, y, x1.cpu().numpy()) <= 1.1e-6
+    assert info1["rel_normres"] <= 1e-6 and info1["outer"] >= 1
+
+
+def test_batch_of_mixed_problems():
+    probs = small_batch(12)
+    plans, ys, ops = [], [], []
+    g = synth.rng(10)
+    for pr in probs:
+        op = oracle_op(pr)
+        y = op.apply(pr.x_true)
+        if pr.dim == 1:
+            y = y + 1e-3 * synth.complex_gaussian(y.size, g) * np.sqrt(voronoi_1d(pr.xi, pr.bandwidth))
+        else:
+            y = y + 1e-3 * synth.complex_gaussian(y.size, g)
+        plans.append(make_plan(pr))
+        ys.append(torch.tensor(y, device="cuda"))
+        ops.append(op)
+    xs = [torch.zeros(p.ncoef, dtype=torch.complex128, device="cuda") for p in plans]
+    infos = gs.gs_solve_batch([p.handle for p in plans], ys, xs, tol=1e-6, maxit=4000)
+    for k, (op, y, x, info) in enumerate(zip(ops, ys, xs, infos)):
+        assert info["status"] == gs.GS_OK, (k, info)
+        r = rel_normres(op, y.cpu().numpy(), x.cpu().numpy())
+        assert r <= 1.1e-6, (k, r, info)
+        # one at a time gives the same x (same kernels, same order)
+        x1, _ = plans[k].solve(y, tol=1e-6, maxit=4000)
+        assert torch.equal(x1, x), k
+
+
+def test_batch_rejects_repeated_plan():
+    pr = small_batch(1)[0]
+    plan = make_plan(pr)
+    y = torch.zeros(plan.M, dtype=torch.complex128, device="cuda")
+    x = torch.zeros(plan.ncoef, dtype=torch.complex128, device="cuda")
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_solve_batch([plan.handle, plan.handle], [y, y], [x, x])
+    assert e.value.status == gs.GS_EINVAL
