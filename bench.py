@@ -156,6 +156,8 @@ def main():
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also time gs_solve_batch on this many problems of the mixed 1D/2D batch workload")
     ap.add_argument("--probe-apply", type=int, default=0,
                     help="only run this many float32 T^H and T applies on the workload (for profilers)")
     args = ap.parse_args()
@@ -297,6 +299,8 @@ def main():
             fit.append(inf["iterations"])
         fp64 = {"value": 1e3 / np.mean(fe), "unit": UNIT, "iterations": fit, "ms_per_step": float(np.mean(fe))}
 
+    batch = batch_bench(args.batch, dev) if args.batch > 0 else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it_ref = fp64["iterations"][0] if fp64 else int(np.median(iters))
@@ -317,9 +321,62 @@ def main():
         "iterations": iters, "converged": ok, "rel_normres": [i["rel_normres"] for i in infos],
         "outer": [i["outer"] for i in infos],
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernel_shares": shares,
-        "fp64_cgls": fp64, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "fp64_cgls": fp64, "batch": batch, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def batch_bench(count, dev):
+    """Mixed batch: half 1D (db2/db4, J 8..13, oversampling 2..4, jittered, Voronoi
+    weights), half 2D (db4, J 6..8, jittered grid or spiral, unit weights); data
+    T x* + 0.1% noise from the library's own float64 forward apply.  Times
+    gs_solve_batch (one graph per problem, 16 streams) against the same problems
+    solved one after another with gs_solve."""
+    import torch
+    import paper_1607_04091_gb300 as gs
+
+    probs = synth.batch_specs(count=count, seed=4004)
+    t0 = time.perf_counter()
+    plans = []
+    for pr in probs:
+        if pr.dim == 1:
+            plans.append(gs.Plan.plan_1d(pr.xi, pr.p, pr.J, bandwidth=pr.bandwidth))
+        else:
+            plans.append(gs.Plan.plan_2d(pr.xi, pr.p, pr.J))
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    g = synth.rng(4005)
+    ys = []
+    for pr, pl in zip(probs, plans):
+        yc = pl.T(torch.tensor(pr.x_true, device=dev)).cpu().numpy()
+        ys.append(torch.tensor(yc + 1e-3 * np.sqrt(np.mean(np.abs(yc) ** 2)) * synth.complex_gaussian(yc.size, g),
+                               device=dev))
+    xs = [torch.zeros(pl.ncoef, dtype=torch.complex128, device=dev) for pl in plans]
+    handles = [pl.handle for pl in plans]
+    gs.gs_solve_batch(handles, ys, xs, tol=TOL, maxit=5000)  # warm-up: builds the per-plan graphs
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush.zero_()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    infos = gs.gs_solve_batch(handles, ys, xs, tol=TOL, maxit=5000)
+    b.record()
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3
+    flush.zero_()
+    torch.cuda.synchronize()
+    a.record()
+    for pl, y, x in zip(plans, ys, xs):
+        gs.gs_solve(pl.handle, y, x, tol=TOL, maxit=5000)
+    b.record()
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    ok = sum(1 for i in infos if i["status"] == gs.GS_OK and i["rel_normres"] <= TOL)
+    return {"problems": count, "value": count / t_batch, "unit": "reconstructions/s", "seconds": t_batch,
+            "one_at_a_time": {"value": count / t_seq, "seconds": t_seq}, "converged": ok,
+            "iterations_total": int(sum(i["iterations"] for i in infos)), "init_s": init_s,
+            "workload": "mixed batch: 1D db2/db4 J 8..13 jittered + 2D db4 J 6..8 jittered/spiral, "
+                        "oversampling 2..4, tol 1e-6, mixed precision"}
 
 
 def probe_apply(reps):

@@ -81,13 +81,13 @@ static void free_graphs(PrecData<R>& D) {
 }
 
 static void free_prec_f(PrecData<float>& D) {
-  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
+  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
 static void free_prec_d(PrecData<double>& D) {
-  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.side, D.part, D.corner,
+  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -170,12 +170,12 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
   const int tile = (dims == 1) ? TILE1 : TILE2;
   const int64_t eff_tile = P->n < tile ? P->n : tile;
   bool nfft_ok = (eff_tile >= mmax) && (P->n >= 2 * mmax);
-  if (dims == 1 && P->n > 8192) nfft_ok = false;  // one-CTA FFT in float64
+  if (dims == 1 && P->n > (1 << 20)) nfft_ok = false;  // four-step FFT: n1, n2 <= 1024
   if (dims == 2 && P->n > 1024) nfft_ok = false;  // float64 column-pass tiles in shared memory
   if (o.direct == 1) P->direct = 1;
   else if (o.direct == 0) {
     if (!nfft_ok) {
-      set_error("NFFT path needs n = sigma 2^J >= 2 m, a tile >= m and n <= %d", dims == 1 ? 8192 : 1024);
+      set_error("NFFT path needs n = sigma 2^J >= 2 m, a tile >= m and n <= %d", dims == 1 ? (1 << 20) : 1024);
       delete h;
       return GS_EUNSUPPORTED;
     }

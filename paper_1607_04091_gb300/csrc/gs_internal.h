@@ -85,6 +85,7 @@ struct PrecData {
   // workspaces
   C<R>* grid = nullptr;   // n^dims (2D: [lx][ly])
   C<R>* hbuf = nullptr;   // 2D: N x n, row j of the x transform ([j][lx])
+  C<R>* ftmp = nullptr;   // 1D, n >= 4096: n, the four-step FFT's intermediate
   C<R>* side = nullptr;   // 2D: [2][2b][n]  (0: x-sides along y, 1: y-sides along x)
   C<R>* part = nullptr;   // spread partials, per work item
   C<R>* corner = nullptr; // 2D: (2b)^2 corner adjoint, 1D: 2b boundary adjoint

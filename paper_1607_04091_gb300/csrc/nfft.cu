@@ -34,7 +34,8 @@ __device__ inline int brev(int i, int logn) { return (int)(__brev((unsigned)i) >
 // In-place radix-2 DIT FFT of nb sequences of length n held in shared memory in
 // bit-reversed order; output in natural order.  tw[k] = exp(-2 pi i k/n).
 template <typename R>
-__device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restrict__ tw, bool inverse) {
+__device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restrict__ tw, bool inverse,
+                         int tws = 1) {
   const int half_total = nb * (n >> 1);
   for (int s = 1; s <= logn; ++s) {
     const int half = 1 << (s - 1);
@@ -46,7 +47,7 @@ __device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restr
       int pos = bt & (half - 1);
       int i0 = seq * n + grp * 2 * half + pos;
       int i1 = i0 + half;
-      C<R> w = tw[pos * step];
+      C<R> w = tw[pos * step * tws];
       if (inverse) w.y = -w.y;
       C<R> a = buf[i0];
       C<R> bb = cmul(buf[i1], w);
@@ -76,6 +77,96 @@ __global__ void k_fwd1d_fft(const C<R>* __restrict__ x, const R* __restrict__ de
   __syncthreads();
   fft_smem<R>(buf, 1, n, logn, tw, false);
   for (int i = threadIdx.x; i < n; i += blockDim.x) grid[i] = buf[i];
+}
+
+// ---------------------------------------------------------------- 1D four-step FFT (large n)
+// n = n1 n2, l = j1 + n1 j2, l' = k2 + n2 k1:
+//   G[l'] = sum_j1 e^{-2 pi i j1 k1/n1} [ e^{-2 pi i j1 k2/n} sum_j2 a[j1 + n1 j2] e^{-2 pi i j2 k2/n2} ]
+// tw holds e^{-2 pi i k/n}, k < n/2 (sub-FFTs of length L use stride n/L).
+template <typename R>
+__device__ inline C<R> tw_full(const C<R>* tw, int64_t k, int64_t n, bool inverse) {
+  k %= n;
+  C<R> w = (k < n / 2) ? tw[k] : tw[k - n / 2];
+  if (k >= n / 2) {
+    w.x = -w.x;
+    w.y = -w.y;
+  }
+  if (inverse) w.y = -w.y;
+  return w;
+}
+
+// forward step 1: CTA per j1; deapodised, zero-padded input column -> B[j1][k2]
+template <typename R>
+__global__ void k_fwd1d_cols(const C<R>* __restrict__ x, const R* __restrict__ deap, int64_t N, int n, int n1,
+                             int n2, int logn2, const C<R>* __restrict__ tw, C<R>* __restrict__ B) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int j1 = blockIdx.x;
+  for (int j2 = threadIdx.x; j2 < n2; j2 += blockDim.x) {
+    const int l = j1 + n1 * j2;
+    const int64_t k = (l < n / 2) ? l : (int64_t)l - n;
+    const int64_t i = k + N / 2;
+    C<R> v = mk<R>(0, 0);
+    if (i >= 0 && i < N) {
+      const R dv = deap[i];
+      if (dv != (R)0) v = cscale(x[i], dv);
+    }
+    buf[brev(j2, logn2)] = v;
+  }
+  __syncthreads();
+  fft_smem<R>(buf, 1, n2, logn2, tw, false, n / n2);
+  for (int k2 = threadIdx.x; k2 < n2; k2 += blockDim.x)
+    B[(int64_t)j1 * n2 + k2] = cmul(buf[k2], tw_full<R>(tw, (int64_t)j1 * k2, n, false));
+}
+
+// forward step 2: CTA per k2; FFT over j1 -> grid[k2 + n2 k1]
+template <typename R>
+__global__ void k_fwd1d_rows(const C<R>* __restrict__ B, int n, int n1, int logn1, int n2,
+                             const C<R>* __restrict__ tw, C<R>* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int k2 = blockIdx.x;
+  for (int j1 = threadIdx.x; j1 < n1; j1 += blockDim.x) buf[brev(j1, logn1)] = B[(int64_t)j1 * n2 + k2];
+  __syncthreads();
+  fft_smem<R>(buf, 1, n1, logn1, tw, false, n / n1);
+  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) grid[k2 + (int64_t)n2 * k1] = buf[k1];
+}
+
+// adjoint step 1: CTA per k2; inverse FFT over k1 of grid[k2 + n2 k1], twiddle -> Cb[k2][j1]
+template <typename R>
+__global__ void k_adj1d_rows(const C<R>* __restrict__ grid, int n, int n1, int logn1, int n2,
+                             const C<R>* __restrict__ tw, C<R>* __restrict__ Cb) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int k2 = blockIdx.x;
+  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) buf[brev(k1, logn1)] = grid[k2 + (int64_t)n2 * k1];
+  __syncthreads();
+  fft_smem<R>(buf, 1, n1, logn1, tw, true, n / n1);
+  for (int j1 = threadIdx.x; j1 < n1; j1 += blockDim.x)
+    Cb[(int64_t)k2 * n1 + j1] = cmul(buf[j1], tw_full<R>(tw, (int64_t)j1 * k2, n, true));
+}
+
+// adjoint step 2: CTA per j1; inverse FFT over k2 -> z at l = j1 + n1 j2, cropped and
+// deapodised; boundary coefficients from the channel sums
+template <typename R>
+__global__ void k_adj1d_cols(const C<R>* __restrict__ Cb, const R* __restrict__ deap, int64_t N, int n, int n1,
+                             int n2, int logn2, const C<R>* __restrict__ tw, const C<R>* __restrict__ bsum, int b,
+                             C<R>* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  const int j1 = blockIdx.x;
+  for (int k2 = threadIdx.x; k2 < n2; k2 += blockDim.x) buf[brev(k2, logn2)] = Cb[(int64_t)k2 * n1 + j1];
+  __syncthreads();
+  fft_smem<R>(buf, 1, n2, logn2, tw, true, n / n2);
+  for (int j2 = threadIdx.x; j2 < n2; j2 += blockDim.x) {
+    const int l = j1 + n1 * j2;
+    const int64_t k = (l < n / 2) ? l : (int64_t)l - n;
+    const int64_t i = k + N / 2;
+    if (i < 0 || i >= N) continue;
+    if (i >= b && i < N - b) z[i] = cscale(buf[j2], deap[i]);
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < 2 * b; i += blockDim.x) z[i < b ? i : N - 1 - (i - b)] = bsum[i];
 }
 
 // KB interpolation + weights + boundary block, one thread per sorted sample
@@ -445,6 +536,7 @@ gs_status set_smem(const void* fn, size_t bytes) {
 }
 
 template <typename R> constexpr int pass_cols() { return 2; }
+constexpr int FOUR_STEP_N = 4096;  // 1D grids from this size use the two-pass FFT
 
 }  // namespace
 
@@ -455,15 +547,19 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
   const int64_t M = P->M;
   const R beta = (R)D.beta;
   if (P->dims == 1) {
-    size_t sh = (size_t)n * sizeof(C<R>);
-    if (sh > 227 * 1024) {
-      set_error("1D grid of %d points does not fit one CTA in this precision", n);
-      return GS_EUNSUPPORTED;
+    if (n >= FOUR_STEP_N) {
+      const int logn1 = logn / 2, logn2 = logn - logn1, n1 = 1 << logn1, n2 = 1 << logn2;
+      GS_LAUNCH(pname<R>("fwd1d_cols<f32>", "fwd1d_cols<f64>"), st,
+                k_fwd1d_cols<R><<<n1, 256, n2 * sizeof(C<R>), st>>>(x, D.deap, N, n, n1, n2, logn2, D.tw, D.ftmp));
+      GS_LAUNCH(pname<R>("fwd1d_rows<f32>", "fwd1d_rows<f64>"), st,
+                k_fwd1d_rows<R><<<n2, 256, n1 * sizeof(C<R>), st>>>(D.ftmp, n, n1, logn1, n2, D.tw, D.grid));
+    } else {
+      size_t sh = (size_t)n * sizeof(C<R>);
+      gs_status s = set_smem<R>((const void*)k_fwd1d_fft<R>, sh);
+      if (s != GS_OK) return s;
+      GS_LAUNCH(pname<R>("fwd1d_fft<f32>", "fwd1d_fft<f64>"), st,
+                k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
     }
-    gs_status s = set_smem<R>((const void*)k_fwd1d_fft<R>, sh);
-    if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("fwd1d_fft<f32>", "fwd1d_fft<f64>"), st,
-              k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
     GS_LAUNCH(pname<R>("interp1d<f32>", "interp1d<f64>"), st,
               k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
                                                              x, N, M, perm, y));
@@ -511,11 +607,20 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     if (b2 > 0)
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
                 k_reduce_chan<R><<<b2, 256, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
-    size_t shf = (size_t)n * sizeof(C<R>);
-    gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
-    if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
-              k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+    if (n >= FOUR_STEP_N) {
+      const int logn1 = logn / 2, logn2 = logn - logn1, n1 = 1 << logn1, n2 = 1 << logn2;
+      GS_LAUNCH(pname<R>("adj1d_rows<f32>", "adj1d_rows<f64>"), st,
+                k_adj1d_rows<R><<<n2, 256, n1 * sizeof(C<R>), st>>>(D.grid, n, n1, logn1, n2, D.tw, D.ftmp));
+      GS_LAUNCH(pname<R>("adj1d_cols<f32>", "adj1d_cols<f64>"), st,
+                k_adj1d_cols<R><<<n1, 256, n2 * sizeof(C<R>), st>>>(D.ftmp, D.deap, N, n, n1, n2, logn2, D.tw,
+                                                                    D.corner, b, z));
+    } else {
+      size_t shf = (size_t)n * sizeof(C<R>);
+      gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
+      if (s != GS_OK) return s;
+      GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
+                k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+    }
   } else {
     const int PW = tile + 2 * m;
     const int wsz = PW * PW + 2 * b2 * PW;
@@ -579,11 +684,20 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     if (b2 > 0)
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
                 k_reduce_chan<R><<<b2, 256, 0, st>>>(part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
-    size_t shf = (size_t)n * sizeof(C<R>);
-    gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
-    if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
-              k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+    if (n >= FOUR_STEP_N) {
+      const int logn1 = logn / 2, logn2 = logn - logn1, n1 = 1 << logn1, n2 = 1 << logn2;
+      GS_LAUNCH(pname<R>("adj1d_rows<f32>", "adj1d_rows<f64>"), st,
+                k_adj1d_rows<R><<<n2, 256, n1 * sizeof(C<R>), st>>>(D.grid, n, n1, logn1, n2, D.tw, D.ftmp));
+      GS_LAUNCH(pname<R>("adj1d_cols<f32>", "adj1d_cols<f64>"), st,
+                k_adj1d_cols<R><<<n1, 256, n2 * sizeof(C<R>), st>>>(D.ftmp, D.deap, N, n, n1, n2, logn2, D.tw,
+                                                                    D.corner, b, z));
+    } else {
+      size_t shf = (size_t)n * sizeof(C<R>);
+      gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
+      if (s != GS_OK) return s;
+      GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
+                k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+    }
   } else {
     const int PW = tile + 2 * m;
     const int wsz = PW * PW + 2 * b2 * PW;

@@ -338,6 +338,7 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
   if (!P->direct) {
     if (dims == 1) {
       GS_TRY(dalloc(&D.grid, (size_t)n));
+      if (n >= 4096) GS_TRY(dalloc(&D.ftmp, (size_t)n));
       D.part_stride = TILE1 + 2 * m + b2;
     } else {
       GS_TRY(dalloc(&D.grid, (size_t)n * n));

@@ -74,6 +74,17 @@ def test_1d_nfft_jittered_wrapping(p, prec):
     check_pair(plan, op, 2**J, M, prec, tol_for(prec, 2 * 2**J), g)
 
 
+@pytest.mark.parametrize("prec", [gs.GS_FP64, gs.GS_FP32])
+def test_1d_nfft_four_step_fft(prec):
+    """J = 11: grid n = 4096 goes through the two-pass (four-step) FFT."""
+    g = synth.rng(79)
+    J, M = 11, 3001
+    xi = g.uniform(-3000, 3000, M)
+    op = Operator1D(Basis1D(4, J), xi)
+    plan = gs.Plan.plan_1d(xi, 4, J, direct=0)
+    check_pair(plan, op, 2**J, M, prec, tol_for(prec, 2 * 2**J), g)
+
+
 def test_1d_direct_matches_nfft_mode():
     g = synth.rng(3)
     J, M = 7, 700
