@@ -162,6 +162,37 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
 gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
                          const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
 
+/* ---- Learned warm start (an addition beside the paper's method) ----------
+ * A residual CNN x0 = u + f(u) on the 2-channel image (real, imaginary part) of
+ * u = T^H y, pixel (j, i) = coefficient i + N j, images NCHW float32.  f is
+ * `depth` 3x3 convolutions (zero padding) with `channels` hidden channels and
+ * ReLU between them; the last layer starts at zero (untrained net = identity).
+ * Training: float32 weights, Adam, mean-squared error; inference: bfloat16 or
+ * float32 weights, float32 accumulation.  H, W multiples of 16; channels 8, 16
+ * or 32; weights initialised He-uniform from `seed`. */
+typedef struct gs_cnn_s* gs_cnn;
+gs_status gs_cnn_create(gs_cnn* out, int H, int W, int channels, int depth, int max_batch, uint64_t seed,
+                        void* stream);
+void gs_cnn_destroy(gs_cnn net);
+/* x0 = u + f(u) for B images (device, B x 2 x H x W float32 each) */
+gs_status gs_cnn_forward(gs_cnn net, const float* u, float* x0, int B, int use_bf16, void* stream);
+/* one Adam step on B (u, target) pairs; mean-squared error of x0 before the step into *loss */
+gs_status gs_cnn_train_step(gs_cnn net, const float* u, const float* target, int B, float lr, double* loss,
+                            void* stream);
+/* loss and gradients (weights then biases, the gs_cnn_weights order) without an update */
+gs_status gs_cnn_gradients(gs_cnn net, const float* u, const float* target, int B, float* grad_host, double* loss);
+/* all weights then all biases, layer by layer ([c_out][c_in][3][3], [c_out]); *count always set */
+gs_status gs_cnn_weights(gs_cnn net, float* host, int64_t* count);
+gs_status gs_cnn_set_weights(gs_cnn net, const float* host, int64_t count);
+
+/* Least squares from the learned warm start: u = T^H y (float32), x0 = rms(u) *
+ * net(u / rms(u)) (bfloat16 weights), then gs_solve from x0 -- or from zero when
+ * ||T^H (y - T x0)|| >= ||T^H y||, the plain method being the fallback and the
+ * judge.  2D plans whose N x N grid is the network's image.  *used_warm_start
+ * (may be NULL) tells which start was taken.  Other arguments as gs_solve. */
+gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, void* x, const gs_solve_opts* opts,
+                           gs_solve_info* info, int* used_warm_start, void* stream);
+
 /* Host-only (no CUDA call): the plan-time constants for p vanishing moments, so
  * they can be checked without a GPU.  h: 2p filter taps h_k, k = -p+1..p, with
  * sum 1 (App. A).  For p >= 2 also the edge matrices of App. A.1, row-major:

@@ -40,7 +40,8 @@ class GsError(RuntimeError):
 
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
-           "gs_apply_TH_noalloc", "gs_solve_batch",
+           "gs_apply_TH_noalloc", "gs_solve_batch", "gs_cnn_create", "gs_cnn_destroy", "gs_cnn_forward",
+           "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
            "gs_last_error_detail"]
 
@@ -75,6 +76,21 @@ def load(path: str = LIB):
     lib.gs_profile.restype = ctypes.c_int
     lib.gs_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_int64]
     lib.gs_profile_report.restype = ctypes.c_int
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.gs_cnn_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_uint64, vp]
+    lib.gs_cnn_destroy.argtypes = [vp]
+    lib.gs_cnn_destroy.restype = None
+    lib.gs_cnn_forward.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.gs_cnn_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, dp, vp]
+    lib.gs_cnn_gradients.argtypes = [vp, vp, vp, ctypes.c_int, fp, dp]
+    lib.gs_cnn_weights.argtypes = [vp, fp, ctypes.POINTER(i64)]
+    lib.gs_cnn_set_weights.argtypes = [vp, fp, i64]
+    lib.gs_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo),
+                                     ctypes.POINTER(ctypes.c_int), vp]
+    for f in ["gs_cnn_create", "gs_cnn_forward", "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights",
+              "gs_cnn_set_weights", "gs_solve_learned"]:
+        getattr(lib, f).restype = ctypes.c_int
     lib.gs_strerror.argtypes = [ctypes.c_int]
     lib.gs_strerror.restype = ctypes.c_char_p
     lib.gs_last_error_detail.restype = ctypes.c_char_p
@@ -279,3 +295,98 @@ class Plan:
                 self.handle = None
         except Exception:
             pass
+
+
+class Cnn:
+    """Owning wrapper of a gs_cnn (residual CNN warm start); images are
+    (B, 2, H, W) float32 CUDA tensors."""
+
+    def __init__(self, H, W, channels=32, depth=6, max_batch=8, seed=1, stream=None):
+        self.H, self.W, self.channels, self.depth, self.max_batch = H, W, channels, depth, max_batch
+        h = ctypes.c_void_p()
+        _check(load().gs_cnn_create(ctypes.byref(h), H, W, channels, depth, max_batch, seed, _stream(stream)),
+               "gs_cnn_create")
+        self.handle = h
+        self.chans = [2] + [channels] * (depth - 1) + [2]
+
+    def _img(self, t, B):
+        import torch
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == B * 2 * self.H * self.W):
+            raise ValueError("expected a contiguous float32 CUDA tensor of shape (B, 2, H, W)")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def forward(self, u, bf16=True, stream=None):
+        import torch
+        B = u.shape[0]
+        out = torch.empty_like(u)
+        _check(load().gs_cnn_forward(self.handle, self._img(u, B), self._img(out, B), B, int(bool(bf16)),
+                                     _stream(stream)), "gs_cnn_forward")
+        return out
+
+    def train_step(self, u, target, lr=1e-3, stream=None):
+        B = u.shape[0]
+        loss = ctypes.c_double()
+        _check(load().gs_cnn_train_step(self.handle, self._img(u, B), self._img(target, B), B, lr, ctypes.byref(loss),
+                                        _stream(stream)), "gs_cnn_train_step")
+        return loss.value
+
+    def gradients(self, u, target):
+        B = u.shape[0]
+        n = ctypes.c_int64()
+        load().gs_cnn_weights(self.handle, None, ctypes.byref(n))
+        g = np.zeros(n.value, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(load().gs_cnn_gradients(self.handle, self._img(u, B), self._img(target, B), B,
+                                       g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)),
+               "gs_cnn_gradients")
+        return loss.value, g
+
+    def weights(self):
+        n = ctypes.c_int64()
+        load().gs_cnn_weights(self.handle, None, ctypes.byref(n))
+        w = np.zeros(n.value, dtype=np.float32)
+        _check(load().gs_cnn_weights(self.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(n)),
+               "gs_cnn_weights")
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(load().gs_cnn_set_weights(self.handle, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), w.size),
+               "gs_cnn_set_weights")
+
+    def unflatten(self, flat):
+        """Split a flat weights-then-biases vector into [(W (co, ci, 3, 3), b (co,))]."""
+        layers, off = [], 0
+        shapes = list(zip(self.chans[:-1], self.chans[1:]))
+        for ci, co in shapes:
+            layers.append(flat[off:off + co * ci * 9].reshape(co, ci, 3, 3))
+            off += co * ci * 9
+        out = []
+        for (ci, co), W in zip(shapes, layers):
+            out.append((W, flat[off:off + co]))
+            off += co
+        return out
+
+    def __del__(self):
+        try:
+            if self.handle:
+                load().gs_cnn_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def gs_solve_learned(plan, net, y, x, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED, max_outer=8, inner_rtol=0.0,
+                     stream=None):
+    """Returns (info dict, used_warm_start)."""
+    import torch
+    _, M, _, nc = gs_plan_sizes(plan)
+    o = GsSolveOpts(tol, maxit, mode, 0, max_outer, inner_rtol)
+    info = GsSolveInfo()
+    used = ctypes.c_int()
+    st = load().gs_solve_learned(plan, net.handle, _dev(y, torch.complex128, M), _dev(x, torch.complex128, nc),
+                                 ctypes.byref(o), ctypes.byref(info), ctypes.byref(used), _stream(stream))
+    if st not in (GS_OK, GS_ENOTCONV):
+        _check(st, "gs_solve_learned")
+    return ({"iterations": info.iterations, "outer": info.outer, "rel_normres": info.rel_normres,
+             "rel_res": info.rel_res, "status": info.status}, bool(used.value))
