@@ -158,6 +158,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--batch", type=int, default=0,
                     help="also time gs_solve_batch on this many problems of the mixed 1D/2D batch workload")
+    ap.add_argument("--learned", type=int, default=0,
+                    help="also train the warm-start CNN on this many method-generated pairs and time "
+                         "zero / adjoint / learned starts on held-out problems")
     ap.add_argument("--probe-apply", type=int, default=0,
                     help="only run this many float32 T^H and T applies on the workload (for profilers)")
     args = ap.parse_args()
@@ -300,6 +303,7 @@ def main():
         fp64 = {"value": 1e3 / np.mean(fe), "unit": UNIT, "iterations": fit, "ms_per_step": float(np.mean(fe))}
 
     batch = batch_bench(args.batch, dev) if args.batch > 0 else None
+    learned = learned_bench(plan, xi, mu, args.learned, 16, dev) if args.learned > 0 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -321,7 +325,7 @@ def main():
         "iterations": iters, "converged": ok, "rel_normres": [i["rel_normres"] for i in infos],
         "outer": [i["outer"] for i in infos],
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernel_shares": shares,
-        "fp64_cgls": fp64, "batch": batch, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "fp64_cgls": fp64, "batch": batch, "learned": learned, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -377,6 +381,72 @@ def batch_bench(count, dev):
             "iterations_total": int(sum(i["iterations"] for i in infos)), "init_s": init_s,
             "workload": "mixed batch: 1D db2/db4 J 8..13 jittered + 2D db4 J 6..8 jittered/spiral, "
                         "oversampling 2..4, tol 1e-6, mixed precision"}
+
+
+def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=6, batch=8, lr=1e-3):
+    """Learned warm start on the radial workload: pairs (T^H y, method solution)
+    from random ellipse and tensor piecewise-smooth phantoms with 1% noise; a
+    6-layer, 32-channel residual CNN trained by the library's kernels; then
+    iterations and time to the 1e-6 tolerance from zero, from the adjoint
+    (the untrained, identity net) and from the trained net on held-out data."""
+    import torch
+    import paper_1607_04091_gb300 as gs
+
+    N = 2**J
+
+    def problem(seed):
+        g = synth.rng(5000 + seed)
+        xs = (synth.ellipse_phantom(N, g) if seed % 2 == 0 else synth.tensor_phantom(N, g)) + 0j
+        yc = plan.T(torch.tensor(xs, device=dev)).cpu().numpy()
+        sig = 0.01 * np.sqrt(np.mean(np.abs(yc) ** 2))
+        return torch.tensor(yc + sig * synth.complex_gaussian(yc.size, g), device=dev)
+
+    t0 = time.perf_counter()
+    U = torch.empty((ntrain, 2, N, N), dtype=torch.float32, device=dev)
+    X = torch.empty_like(U)
+    for k in range(ntrain):
+        y = problem(k)
+        x, _ = plan.solve(y, tol=TOL, maxit=5000)
+        u, xi_ = gs.gs_cnn_pair(plan.handle, y, x)
+        U[k].copy_(u[0])
+        X[k].copy_(xi_[0])
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = gs.Cnn(N, N, channels=32, depth=6, max_batch=batch, seed=11)
+    ident = gs.Cnn(N, N, channels=32, depth=6, max_batch=1, seed=11)
+    g = np.random.default_rng(12)
+    losses = []
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        order = g.permutation(ntrain)
+        for s0 in range(0, ntrain - batch + 1, batch):
+            idx = torch.tensor(order[s0:s0 + batch], device=dev)
+            losses.append(net.train_step(U[idx].contiguous(), X[idx].contiguous(), lr=lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"zero": [], "adjoint": [], "learned": []}
+    used = 0
+    for k in range(ntest):
+        y = problem(100000 + k)
+        for key in res:
+            x = torch.zeros(plan.ncoef, dtype=torch.complex128, device=dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if key == "zero":
+                info = gs.gs_solve(plan.handle, y, x, tol=TOL, maxit=5000)
+            else:
+                info, u = gs.gs_solve_learned(plan.handle, ident if key == "adjoint" else net, y, x, tol=TOL,
+                                              maxit=5000)
+                used += int(u and key == "learned")
+            b.record()
+            torch.cuda.synchronize()
+            res[key].append((info["iterations"], a.elapsed_time(b), info["rel_normres"]))
+    summ = {k: {"iterations": float(np.mean([r[0] for r in v])), "ms": float(np.mean([r[1] for r in v])),
+                "max_rel_normres": float(max(r[2] for r in v))} for k, v in res.items()}
+    return {"train_pairs": ntrain, "test_problems": ntest, "epochs": epochs, "batch": batch,
+            "loss_first": losses[0], "loss_last": float(np.mean(losses[-max(1, ntrain // batch):])),
+            "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ,
+            "net": "6 conv3x3 layers 2-32-32-32-32-32-2, ReLU, residual, bf16 inference weights"}
 
 
 def probe_apply(reps):

@@ -185,6 +185,12 @@ gs_status gs_cnn_gradients(gs_cnn net, const float* u, const float* target, int 
 gs_status gs_cnn_weights(gs_cnn net, float* host, int64_t* count);
 gs_status gs_cnn_set_weights(gs_cnn net, const float* host, int64_t count);
 
+/* A training pair for the network: u_img = image of u / rms(u), u = T^H y
+ * (float32 adjoint), and, when x and x_img are non-NULL, x_img = image of
+ * x / rms(u) (x: ncoef complex128, e.g. the method's reconstruction).  Images are
+ * 2 x N x N float32 on the device. */
+gs_status gs_cnn_pair(gs_plan plan, const void* y, const void* x, float* u_img, float* x_img, void* stream);
+
 /* Least squares from the learned warm start: u = T^H y (float32), x0 = rms(u) *
  * net(u / rms(u)) (bfloat16 weights), then gs_solve from x0 -- or from zero when
  * ||T^H (y - T x0)|| >= ||T^H y||, the plain method being the fallback and the

@@ -41,7 +41,7 @@ class GsError(RuntimeError):
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
            "gs_apply_TH_noalloc", "gs_solve_batch", "gs_cnn_create", "gs_cnn_destroy", "gs_cnn_forward",
-           "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned",
+           "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned", "gs_cnn_pair",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
            "gs_last_error_detail"]
 
@@ -88,8 +88,9 @@ def load(path: str = LIB):
     lib.gs_cnn_set_weights.argtypes = [vp, fp, i64]
     lib.gs_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo),
                                      ctypes.POINTER(ctypes.c_int), vp]
+    lib.gs_cnn_pair.argtypes = [vp, vp, vp, vp, vp, vp]
     for f in ["gs_cnn_create", "gs_cnn_forward", "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights",
-              "gs_cnn_set_weights", "gs_solve_learned"]:
+              "gs_cnn_set_weights", "gs_solve_learned", "gs_cnn_pair"]:
         getattr(lib, f).restype = ctypes.c_int
     lib.gs_strerror.argtypes = [ctypes.c_int]
     lib.gs_strerror.restype = ctypes.c_char_p
@@ -390,3 +391,16 @@ def gs_solve_learned(plan, net, y, x, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED,
         _check(st, "gs_solve_learned")
     return ({"iterations": info.iterations, "outer": info.outer, "rel_normres": info.rel_normres,
              "rel_res": info.rel_res, "status": info.status}, bool(used.value))
+
+
+def gs_cnn_pair(plan, y, x=None, stream=None):
+    """(u_img, x_img) float32 (1, 2, N, N) images: T^H y / rms and x / the same rms."""
+    import torch
+    _, M, N, nc = gs_plan_sizes(plan)
+    u = torch.empty((1, 2, N, N), dtype=torch.float32, device=y.device)
+    xi = torch.empty_like(u) if x is not None else None
+    _check(load().gs_cnn_pair(plan, _dev(y, torch.complex128, M),
+                              _dev(x, torch.complex128, nc) if x is not None else None,
+                              ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(xi.data_ptr()) if xi is not None else None,
+                              _stream(stream)), "gs_cnn_pair")
+    return u, xi

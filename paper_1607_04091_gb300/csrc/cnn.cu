@@ -614,3 +614,32 @@ extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, v
   if (!warm) GS_CUDA(cudaMemsetAsync(x, 0, nc * sizeof(double2), st));
   return gs_solve(plan, y, x, &o, info, stream);
 }
+
+extern "C" gs_status gs_cnn_pair(gs_plan plan, const void* y, const void* x, float* u_img, float* x_img,
+                                 void* stream) {
+  if (!plan || !y || !u_img) {
+    set_error("gs_cnn_pair: plan, y and u_img must be non-NULL");
+    return GS_EINVAL;
+  }
+  Plan* P = &plan->P;
+  if (P->dims != 2) {
+    set_error("gs_cnn_pair: 2D plans only");
+    return GS_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nc = P->ncoef, M = P->M;
+  PrecData<float>& F = P->f;
+  GS_TRY(gather_sorted<double>(P, (const double2*)y, (double2*)P->y64, st));
+  k_c128_to_c64<<<blocks(M), 256, 0, st>>>((const double2*)P->y64, F.vr, M);
+  GS_TRY(apply_TH<float>(P, F, F.vr, F.vs, nullptr, st));
+  double* sq = P->scal + 40;
+  float* scale = reinterpret_cast<float*>(P->scal + 42);
+  k_sq1<<<1, 1024, 0, st>>>(F.vs, nc, sq);
+  k_coef_to_image<<<blocks(nc), 256, 0, st>>>(F.vs, nc, sq, u_img, scale);
+  if (x && x_img) {
+    k_c128_to_c64<<<blocks(nc), 256, 0, st>>>((const double2*)x, F.vz, nc);
+    k_coef_to_image<<<blocks(nc), 256, 0, st>>>(F.vz, nc, sq, x_img, scale);  // same scale as u
+  }
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}

@@ -106,6 +106,14 @@ def ellipse_phantom(N: int, g: np.random.Generator, count: int = 10) -> np.ndarr
     return (img / N).ravel()
 
 
+def tensor_phantom(N: int, g: np.random.Generator) -> np.ndarray:
+    """Outer product of two random piecewise-smooth profiles (scaled like the
+    ellipse phantom), x-fastest."""
+    a = piecewise_smooth(N, g) * np.sqrt(N)
+    b = piecewise_smooth(N, g) * np.sqrt(N)
+    return (np.outer(b, a) / N).ravel()
+
+
 def complex_gaussian(n: int, g: np.random.Generator) -> np.ndarray:
     """Unit-variance circular complex normal values (variance 1/2 in Re and Im)."""
     return (g.standard_normal(n) + 1j * g.standard_normal(n)) / np.sqrt(2.0)
