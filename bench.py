@@ -383,7 +383,7 @@ def batch_bench(count, dev):
                         "oversampling 2..4, tol 1e-6, mixed precision"}
 
 
-def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=6, batch=8, lr=1e-3):
+def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3):
     """Learned warm start on the radial workload: pairs (T^H y, method solution)
     from random ellipse and tensor piecewise-smooth phantoms with 1% noise; a
     6-layer, 32-channel residual CNN trained by the library's kernels; then

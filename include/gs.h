@@ -126,7 +126,8 @@ typedef struct {
   double tol;     /* stop when ||T^H (y - T x)|| <= tol * ||T^H y|| [1e-6] */
   int maxit;      /* total CGLS iteration cap [1000] */
   int mode;       /* gs_solve_mode [GS_SOLVE_MIXED] */
-  int x0_given;   /* 1: x holds a starting guess on entry; 0: start from x = 0 [0] */
+  int x0_given;   /* 1: x holds a starting guess on entry, kept only if ||T^H (y - T x0)|| <
+                     ||T^H y|| (else the solve starts from x = 0); 0: start from x = 0 [0] */
   int max_outer;  /* refinement passes in GS_SOLVE_MIXED [8] */
   double inner_rtol; /* GS_SOLVE_MIXED: a pass stops when its ||T^H (r - T d)|| falls
                         by this factor (or below tol ||T^H y|| / 2); 0 = default [1e-4] */
@@ -151,8 +152,8 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
                    gs_solve_info* info, void* stream);
 
 /* B independent least-squares solves (one plan each, plans distinct) with the
- * options of gs_solve.  Each GS_SOLVE_MIXED solve with tol >= 1e-7 and no start
- * guess runs as one CUDA graph (nested while-conditional nodes: refinement
+ * options of gs_solve.  Each GS_SOLVE_MIXED solve with tol >= 1e-7 runs as one
+ * CUDA graph (nested while-conditional nodes: refinement
  * passes around CG iterations, float64 residual and stop test on the device);
  * the B graphs are launched round-robin on 16 library-owned streams ordered
  * after `stream`, with no host synchronisation until all have finished.  Other

@@ -100,7 +100,8 @@ static void free_plan(Plan* P) {
     if (p) cudaFree(p);
   free_graphs(P->d);
   free_graphs(P->f);
-  if (P->solve_exec) cudaGraphExecDestroy(P->solve_exec);
+  for (int i = 0; i < 2; ++i)
+    if (P->solve_exec[i]) cudaGraphExecDestroy(P->solve_exec[i]);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   free_prec_d(P->d);
   free_prec_f(P->f);

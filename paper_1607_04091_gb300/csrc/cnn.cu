@@ -597,22 +597,18 @@ extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, v
   GS_CUDA(cudaGetLastError());
   GS_TRY(gs_cnn_forward(N, img_in, img_out, 1, 1, st));
   k_image_to_coef<<<blocks(nc), 256, 0, st>>>(img_out, nc, scale, (double2*)x);
-  // fallback: keep x0 only if ||T^H (y - T x0)|| < ||T^H y|| (both float32 adjoints)
-  GS_TRY(apply_T<double>(P, P->d, (const double2*)x, P->d.vq, nullptr, st));
-  k_res_c128<<<blocks(M), 256, 0, st>>>((const double2*)P->y64, P->d.vq, F.vr, M);
-  GS_TRY(apply_TH<float>(P, F, F.vr, F.vz, nullptr, st));
-  k_sq1<<<1, 1024, 0, st>>>(F.vz, nc, sq + 1);
   GS_CUDA(cudaGetLastError());
-  double h[2];
-  GS_CUDA(cudaMemcpyAsync(h, sq, sizeof(h), cudaMemcpyDeviceToHost, st));
-  GS_CUDA(cudaStreamSynchronize(st));
-  const bool warm = h[1] < h[0];
-  if (used_warm_start) *used_warm_start = warm ? 1 : 0;
+  // solve from x0; the solve keeps x0 only if ||T^H (y - T x0)|| < ||T^H y|| (else zero start)
   gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
   if (opts) o = *opts;
-  o.x0_given = warm ? 1 : 0;
-  if (!warm) GS_CUDA(cudaMemsetAsync(x, 0, nc * sizeof(double2), st));
-  return gs_solve(plan, y, x, &o, info, stream);
+  o.x0_given = 1;
+  gs_status r = gs_solve(plan, y, x, &o, info, stream);
+  if (used_warm_start) {
+    double w = 1.0;
+    cudaMemcpy(&w, P->scal + 32, sizeof(double), cudaMemcpyDeviceToHost);  // the solver's kept-start flag
+    *used_warm_start = (w != 0.0) ? 1 : 0;
+  }
+  return r;
 }
 
 extern "C" gs_status gs_cnn_pair(gs_plan plan, const void* y, const void* x, float* u_img, float* x_img,

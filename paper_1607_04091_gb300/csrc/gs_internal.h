@@ -130,7 +130,7 @@ struct Plan {
   double* r64 = nullptr;    // M, FP64 residual (complex128)
   double* x64 = nullptr;    // ncoef complex128 accumulator
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
-  cudaGraphExec_t solve_exec = nullptr;  // whole mixed solve as one graph
+  cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};  // whole mixed solve as one graph [zero, given start]
   bool solve_graph_failed = false;
 };
 

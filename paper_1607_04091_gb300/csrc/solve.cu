@@ -25,7 +25,8 @@ namespace {
 constexpr int RED_BLOCKS = 512;
 enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
 // scalars of the device-side mixed solve (solve graph)
-enum { G_TOL2 = 20, G_MAXIT, G_MAXOUT, G_IRTOL2, G_HB2, G_HY2, G_THR2, G_NS2, G_OUTER, G_TOTAL, G_NR2, G_STOP };
+enum { G_TOL2 = 20, G_MAXIT, G_MAXOUT, G_IRTOL2, G_HB2, G_HY2, G_THR2, G_NS2, G_OUTER, G_TOTAL, G_NR2, G_STOP,
+       G_WARM };
 enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
 
 template <typename T> __device__ inline double sqn(T v) { return (double)v.x * v.x + (double)v.y * v.y; }
@@ -474,7 +475,35 @@ gs_status add_while(cudaGraph_t parent, cudaGraphNode_t* dep, cudaGraphCondition
   return GS_OK;
 }
 
-gs_status build_solve_graph(Plan* P, cudaStream_t st, cudaGraphExec_t* out) {
+__global__ void k_set_ns2(double* scal) { scal[G_NS2] = scal[S_TMP]; }
+__global__ void k_set_scal(double* scal, int slot, double v) { scal[slot] = v; }
+
+// warm start worse than zero (||T^H r0|| >= ||T^H y||): restart from x = 0, r = y,
+// s = s_y (kept in vz), the plain method being the fallback
+__global__ void k_fallback_zero(double* scal, double2* __restrict__ x, double2* __restrict__ r,
+                                const double2* __restrict__ y, float2* __restrict__ s, const float2* __restrict__ sy,
+                                int64_t nc, int64_t M) {
+  if (!(scal[S_TMP] >= scal[G_HB2])) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc + M; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nc) {
+      x[i] = make_double2(0.0, 0.0);
+      s[i] = sy[i];
+    } else {
+      r[i - nc] = y[i - nc];
+    }
+  }
+}
+__global__ void k_fallback_scalars(double* scal) {
+  if (scal[S_TMP] >= scal[G_HB2]) {
+    scal[S_TMP] = scal[G_HB2];
+    scal[G_WARM] = 0.0;
+  } else {
+    scal[G_WARM] = 1.0;
+  }
+  scal[G_NS2] = scal[S_TMP];
+}
+
+gs_status build_solve_graph(Plan* P, bool with_x0, cudaStream_t st, cudaGraphExec_t* out) {
   cudaStream_t cs = P->cap_stream;
   PrecData<float>& F = P->f;
   const int64_t nc = P->ncoef, M = P->M;
@@ -497,10 +526,18 @@ gs_status build_solve_graph(Plan* P, cudaStream_t st, cudaGraphExec_t* out) {
   cudaGraphNode_t n_setup, n_oenter, n_outer, n_final;
   GS_TRY(add_child(G, nullptr, cs, [&](cudaStream_t c) -> gs_status {
     GS_TRY(norm2_into<double>(P, (const double2*)P->y64, M, G_HY2, nullptr, c));
-    GS_CUDA(cudaMemsetAsync(P->x64, 0, nc * sizeof(double2), c));
+    if (!with_x0) GS_CUDA(cudaMemsetAsync(P->x64, 0, nc * sizeof(double2), c));
     k_copy<double><<<grid_for(M), 256, 0, c>>>((double2*)P->r64, (const double2*)P->y64, M);
-    GS_TRY(adjoint_of_residual<float>(P, F, c));
+    GS_TRY(adjoint_of_residual<float>(P, F, c));  // ||T^H y||^2, the scale of the stop test
     k_solve_setup<<<1, 1, 0, c>>>(P->scal, P->flag);
+    if (with_x0) {  // r = y - T x0 (float64) and its stop-test value; zero start if not better
+      k_copy<float><<<grid_for(nc), 256, 0, c>>>(F.vz, F.vs, nc);  // T^H y, for the fallback
+      GS_TRY(residual64(P, c));
+      GS_TRY(adjoint_of_residual<float>(P, F, c));
+      k_fallback_zero<<<grid_for(nc + M), 256, 0, c>>>(P->scal, (double2*)P->x64, (double2*)P->r64,
+                                                       (const double2*)P->y64, F.vs, F.vz, nc, M);
+      k_fallback_scalars<<<1, 1, 0, c>>>(P->scal);
+    }
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   }, &n_setup));
@@ -547,19 +584,21 @@ gs_status build_solve_graph(Plan* P, cudaStream_t st, cudaGraphExec_t* out) {
 // mixed solve through the cached solve graph; y_user and x_user as in gs_solve
 gs_status launch_solve_graph(Plan* P, const double* y_user, double* x_user, const gs_solve_opts& o,
                              cudaStream_t st) {
-  if (!P->solve_exec) {
-    gs_status s = build_solve_graph(P, st, &P->solve_exec);
+  const int gi = o.x0_given ? 1 : 0;
+  if (!P->solve_exec[gi]) {
+    gs_status s = build_solve_graph(P, gi == 1, st, &P->solve_exec[gi]);
     if (s != GS_OK) {
-      P->solve_exec = nullptr;
+      P->solve_exec[gi] = nullptr;
       P->solve_graph_failed = true;
       return s;
     }
   }
+  if (o.x0_given) GS_CUDA(cudaMemcpyAsync(P->x64, x_user, P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   GS_TRY(gather_sorted<double>(P, (const double2*)y_user, (double2*)P->y64, st));
   k_set_params<<<1, 1, 0, st>>>(P->scal, o.tol * o.tol, (double)o.maxit, (double)o.max_outer,
                                 o.inner_rtol * o.inner_rtol);
   GS_CUDA(cudaGetLastError());
-  GS_CUDA(cudaGraphLaunch(P->solve_exec, st));
+  GS_CUDA(cudaGraphLaunch(P->solve_exec[gi], st));
   GS_CUDA(cudaMemcpyAsync(x_user, P->x64, P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   return GS_OK;
 }
@@ -586,8 +625,7 @@ gs_status graph_solve_info(Plan* P, const gs_solve_opts& o, gs_solve_info* info)
 
 bool graph_solve_ok(Plan* P, const gs_solve_opts& o) {
   static const bool no_graphs = std::getenv("GS_NO_GRAPHS") != nullptr;
-  return o.mode == GS_SOLVE_MIXED && !o.x0_given && o.tol >= 1e-7 && !prof_on() && !no_graphs &&
-         !P->solve_graph_failed;
+  return o.mode == GS_SOLVE_MIXED && o.tol >= 1e-7 && !prof_on() && !no_graphs && !P->solve_graph_failed;
 }
 
 }  // namespace
@@ -634,8 +672,18 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
   const int check = 4;
   int total = 0, stop = F_RUN;
   double ns2 = hb2;
+  GS_LAUNCH("solve_set_scal", st, k_set_scal<<<1, 1, 0, st>>>(P->scal, G_WARM, o.x0_given ? 1.0 : 0.0));
   if (o.mode == GS_SOLVE_FP64) {
-    if (o.x0_given) GS_TRY(adjoint_of_residual<double>(P, P->d, st));
+    if (o.x0_given) {
+      GS_TRY(adjoint_of_residual<double>(P, P->d, st));
+      if (read_scal(P, S_TMP, st, &err) >= hb2) {  // warm start not better than zero: zero start
+        GS_CUDA(cudaMemsetAsync(x64, 0, nc * sizeof(double2), st));
+        GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(M), 256, 0, st>>>((double2*)P->r64, y64, M));
+        GS_TRY(adjoint_of_residual<double>(P, P->d, st));
+        GS_LAUNCH("solve_set_scal", st, k_set_scal<<<1, 1, 0, st>>>(P->scal, G_WARM, 0.0));
+      }
+      if (err != GS_OK) return err;
+    }
     // D.vr holds r, D.vs = T^H r, scal[S_TMP] = ||T^H r||^2
     GS_TRY(cgls_pass<double>(P, P->d, thr2, o.maxit, check, false, st, &total, &stop));
     GS_LAUNCH("solve_addto", st, k_addto<double><<<grid_for(nc), 256, 0, st>>>(x64, P->d.vx, nc));
@@ -662,6 +710,12 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
       return err;
     };
     if (o.x0_given || hi) GS_TRY(check_value());
+    if (o.x0_given && ns2 >= hb2) {  // warm start not better than zero: zero start
+      GS_CUDA(cudaMemsetAsync(x64, 0, nc * sizeof(double2), st));
+      GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(M), 256, 0, st>>>((double2*)P->r64, y64, M));
+      GS_TRY(check_value());
+      GS_LAUNCH("solve_set_scal", st, k_set_scal<<<1, 1, 0, st>>>(P->scal, G_WARM, 0.0));
+    }
     for (int outer = 0; outer < o.max_outer; ++outer) {
       if (ns2 <= thr2 || total >= o.maxit) break;
       double thr_pass = std::max(0.25 * thr2, o.inner_rtol * o.inner_rtol * ns2);

@@ -86,3 +86,17 @@ def test_batch_rejects_repeated_plan():
     with pytest.raises(gs.GsError) as e:
         gs.gs_solve_batch([plan.handle, plan.handle], [y, y], [x, x])
     assert e.value.status == gs.GS_EINVAL
+
+
+def test_graph_solve_from_given_start():
+    pr = small_batch(4)[2]
+    op = oracle_op(pr)
+    g = synth.rng(11)
+    y = op.apply(pr.x_true) + 1e-3 * synth.complex_gaussian(op.M, g)
+    plan = make_plan(pr)
+    x, info0 = plan.solve(torch.tensor(y, device="cuda"), tol=1e-6)
+    x0 = 0.9 * x  # a start 10% off the solution
+    x1, info1 = plan.solve(torch.tensor(y, device="cuda"), x=x0.clone(), tol=1e-6, x0_given=True)
+    assert info1["status"] == gs.GS_OK
+    assert rel_normres(op, y, x1.cpu().numpy()) <= 1.1e-6
+    assert info1["iterations"] < info0["iterations"]
