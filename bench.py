@@ -39,7 +39,7 @@ WORKLOAD = ("2D db4 J=8 (256x256 coefficients), radial 256 spokes x 1024 points 
 ORACLE_SAMPLE = 4096  # rows of T the CPU oracle applies per timed sample
 # FP64 CGLS iterations of this workload (the oracle's CGLS does the same arithmetic);
 # the GPU arm measures it live, the reference arm uses this recorded count.
-FP64_ITERS_RECORDED = None
+FP64_ITERS_RECORDED = 224  # GB300, float64 CGLS on this workload (bench fp64_cgls.iterations)
 
 
 def log(*a):
@@ -477,7 +477,7 @@ def reference_arm(args, rank):
     if rank != 0:
         return
     xi, mu, xstar, noise = workload()
-    it_ref = FP64_ITERS_RECORDED or 150
+    it_ref = FP64_ITERS_RECORDED
     y = np.zeros(xi.shape[0], dtype=np.complex128)
     for _ in range(max(0, args.warmup)):
         pass

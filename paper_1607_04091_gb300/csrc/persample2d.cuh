@@ -6,6 +6,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -40,7 +41,7 @@ __device__ inline int bcol(int k, int b, int N) { return (k < b) ? k : N - 1 - (
 // W x W interior taps, B2 x W taps of each side and B2^2 corner terms:
 //   y = wx wy v_int + wy sum_k bx_k v_xside_k + wx sum_k by_k v_yside_k + sum bx by X
 template <typename R, int W, int B2>
-__global__ void __launch_bounds__(128, 8) k_interp2d(
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
     const int32_t* __restrict__ work, const int32_t* __restrict__ fl, const R* __restrict__ frac,
     const R* __restrict__ win, const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b_rt,
     const C<R>* __restrict__ grid, const C<R>* __restrict__ hbuf, const C<R>* __restrict__ side, int n, R beta,
@@ -259,6 +260,228 @@ __global__ void __launch_bounds__(256) k_spread2d(
   }
 }
 
+// ---------------------------------------------------------------- tensor-core spread
+// float32, W = 8 taps, 2b = 8 boundary columns, 16 x 16 tiles.  For one work item
+// every output of the spread is a sum over its samples of outer products:
+//   P[x][y]   += (v_s wx_s[x - px_s]) wy_s[y - py_s]      interior, v = u conj(wx wy)
+//   S0[k][y]  += v0_s[k] wy_s[y - py_s]                    x-sides,  v0 = u conj(bx_k) conj(wy)
+//   S1[k][x]  += v1_s[k] wx_s[x - px_s]                    y-sides,  v1 = u conj(wx) conj(by_k)
+//   Cc[kx][ky]+= A_s[kx] conj(by_s[ky])                     corners,  A = u conj(bx)
+// i.e. GEMMs with K = samples.  Phase 1 (thread per sample) writes a batch of 32
+// samples as dense operand rows in shared memory; phase 2 accumulates the output
+// tiles in registers with mma.sync m16n8k8 TF32 using the 3xTF32 split
+// (a_hi b_hi + a_hi b_lo + a_lo b_hi, float32-level accuracy).  Output: the same
+// partial-tile layout as k_spread2d.
+namespace tc {
+constexpr int SBT = 32;         // samples per batch (the K of one round)
+constexpr int LD32 = 40;        // row stride of 32-wide operands (bank-conflict free fragments)
+constexpr int LD16 = 24;        // row stride of 16- and 8-wide operands
+
+__device__ inline uint32_t tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ inline void split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32(x);
+  lo = tf32(x - __uint_as_float(hi));
+}
+__device__ inline void mma(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ inline void mma3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
+                            const uint32_t* bl) {
+  mma(c, ah, bh);
+  mma(c, ah, bl);
+  mma(c, al, bh);
+}
+// A fragment (16 x 8, rows m0.., k-columns k0..) from an operand stored [k][m]
+__device__ inline void load_a(const float* A, int ld, int m0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+  split(A[(k0 + t) * ld + m0 + g], hi[0], lo[0]);
+  split(A[(k0 + t) * ld + m0 + g + 8], hi[1], lo[1]);
+  split(A[(k0 + t + 4) * ld + m0 + g], hi[2], lo[2]);
+  split(A[(k0 + t + 4) * ld + m0 + g + 8], hi[3], lo[3]);
+}
+// B fragment (8 x 8, k-rows k0.., columns n0..) from an operand stored [k][n]
+__device__ inline void load_b(const float* B, int ld, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+  split(B[(k0 + t) * ld + n0 + g], hi[0], lo[0]);
+  split(B[(k0 + t + 4) * ld + n0 + g], hi[1], lo[1]);
+}
+}  // namespace tc
+
+static __global__ void __launch_bounds__(128) k_spread2d_tc(
+    const int32_t* __restrict__ work, const int32_t* __restrict__ fl, const float* __restrict__ win,
+    const float2* __restrict__ w, const float2* __restrict__ bf, const float2* __restrict__ u,
+    const int32_t* __restrict__ perm, int64_t M, int nbx, float2* __restrict__ part, int64_t stride) {
+  using namespace tc;
+  constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
+  extern __shared__ __align__(16) float sm[];
+  float* Ar = sm;                    // [SBT][LD32]  (v wx) real part, rows x = px + a
+  float* Ai = Ar + SBT * LD32;       // imaginary part
+  float* By = Ai + SBT * LD32;       // wy at columns y = py + c
+  float* Bx = By + SBT * LD32;       // wx at columns x = px + a
+  float* V0r = Bx + SBT * LD32;      // [SBT][LD16] x-side coefficients
+  float* V0i = V0r + SBT * LD16;
+  float* V1r = V0i + SBT * LD16;     // y-side coefficients
+  float* V1i = V1r + SBT * LD16;
+  float* Kr = V1i + SBT * LD16;      // A = u conj(bx)
+  float* Ki = Kr + SBT * LD16;
+  float* Cr = Ki + SBT * LD16;       // conj(by)
+  float* Ci = Cr + SBT * LD16;
+  constexpr int NST = 4 * SBT * LD32 + 8 * SBT * LD16;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
+  // accumulators: [re/im or second product][n-block 0..3][4]
+  float acc[2][4][4];
+  float cacc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+      if (j < 2)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cacc[j][q] = 0.0f;
+    }
+  // operands start at zero; afterwards each thread clears only the windows it wrote
+  for (int i = threadIdx.x; i < NST; i += blockDim.x) sm[i] = 0.0f;
+  int prev_px = -1, prev_py = -1;
+  for (int sb = s0; sb < s1; sb += SBT) {
+    const int nb = min(SBT, s1 - sb);
+    if (threadIdx.x < SBT && prev_px >= 0) {
+      const int j = threadIdx.x;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        Ar[j * LD32 + prev_px + a] = 0.0f;
+        Ai[j * LD32 + prev_px + a] = 0.0f;
+        Bx[j * LD32 + prev_px + a] = 0.0f;
+        By[j * LD32 + prev_py + a] = 0.0f;
+      }
+      if (j >= nb) {  // no sample in this slot now: clear its boundary rows too
+#pragma unroll
+        for (int k = 0; k < B2; ++k) {
+          V0r[j * LD16 + k] = V0i[j * LD16 + k] = V1r[j * LD16 + k] = V1i[j * LD16 + k] = 0.0f;
+          Kr[j * LD16 + k] = Ki[j * LD16 + k] = Cr[j * LD16 + k] = Ci[j * LD16 + k] = 0.0f;
+        }
+      }
+      prev_px = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      const int j = threadIdx.x, s = sb + j;
+      const float2 us = u[perm ? perm[s] : s];
+      const int px = fl[s] - ox + 1, py = fl[M + s] - oy + 1;
+      const float* wxp = win + ((int64_t)s * 2) * W;
+      const float* wyp = wxp + W;
+      const float2 wxs = w[s], wys = w[M + s];
+      const float2 vi = cmulc(cmulc(us, wxs), wys);
+      const float2 uwx = cmulc(us, wxs);
+      prev_px = px;
+      prev_py = py;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const float wa = __ldg(wxp + a), wc = __ldg(wyp + a);
+        Ar[j * LD32 + px + a] = vi.x * wa;
+        Ai[j * LD32 + px + a] = vi.y * wa;
+        Bx[j * LD32 + px + a] = wa;
+        By[j * LD32 + py + a] = wc;
+      }
+#pragma unroll
+      for (int k = 0; k < B2; ++k) {
+        const float2 bxk = bf[(int64_t)s * B2 + k], byk = bf[(M + s) * B2 + k];
+        const float2 ak = cmulc(us, bxk);
+        const float2 v0 = cmulc(ak, wys);
+        const float2 v1 = cmulc(uwx, byk);
+        V0r[j * LD16 + k] = v0.x;
+        V0i[j * LD16 + k] = v0.y;
+        V1r[j * LD16 + k] = v1.x;
+        V1i[j * LD16 + k] = v1.y;
+        Kr[j * LD16 + k] = ak.x;
+        Ki[j * LD16 + k] = ak.y;
+        Cr[j * LD16 + k] = byk.x;
+        Ci[j * LD16 + k] = -byk.y;
+      }
+    }
+    __syncthreads();
+    // phase 2: warp 0/1 interior rows 0-15 / 16-31; warp 2 x-sides (+ corners with A = Kr);
+    // warp 3 y-sides (+ corners with A = Ki)
+    const float* A0 = (wid < 2) ? Ar : (wid == 2 ? V0r : V1r);
+    const float* A1 = (wid < 2) ? Ai : (wid == 2 ? V0i : V1i);
+    const int lda = (wid < 2) ? LD32 : LD16;
+    const int m0 = (wid == 1) ? 16 : 0;
+    const float* Bm = (wid == 3) ? Bx : By;
+    const float* Ka = (wid == 2) ? Kr : Ki;
+    for (int k0 = 0; k0 < SBT; k0 += 8) {
+      uint32_t a0h[4], a0l[4], a1h[4], a1l[4];
+      load_a(A0, lda, m0, k0, lane, a0h, a0l);
+      load_a(A1, lda, m0, k0, lane, a1h, a1l);
+#pragma unroll
+      for (int nbk = 0; nbk < 4; ++nbk) {
+        uint32_t bh[2], bl[2];
+        load_b(Bm, LD32, nbk * 8, k0, lane, bh, bl);
+        mma3(acc[0][nbk], a0h, a0l, bh, bl);
+        mma3(acc[1][nbk], a1h, a1l, bh, bl);
+      }
+      if (wid >= 2) {
+        uint32_t kh[4], kl[4], ch[2], cl[2];
+        load_a(Ka, LD16, 0, k0, lane, kh, kl);
+        load_b(Cr, LD16, 0, k0, lane, ch, cl);
+        mma3(cacc[0], kh, kl, ch, cl);
+        load_b(Ci, LD16, 0, k0, lane, ch, cl);
+        mma3(cacc[1], kh, kl, ch, cl);
+      }
+    }
+    __syncthreads();
+  }
+  // write the partial tile: P | S0 | S1 | corners
+  const int g = lane >> 2, t = lane & 3;
+  float2* out = part + blockIdx.x * stride;
+  float* cs = sm;  // corner products exchanged between warps 2 and 3: [2 warps][2][16][8]
+  if (wid < 2) {
+#pragma unroll
+    for (int nbk = 0; nbk < 4; ++nbk)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int x = (wid == 1 ? 16 : 0) + g + ((q & 2) ? 8 : 0), y = nbk * 8 + 2 * t + (q & 1);
+        if (x < PW && y < PW) out[x * PW + y] = make_float2(acc[0][nbk][q], acc[1][nbk][q]);
+      }
+  } else {
+    float2* S = out + PW * PW + (wid == 3 ? B2 * PW : 0);
+#pragma unroll
+    for (int nbk = 0; nbk < 4; ++nbk)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = g + ((q & 2) ? 8 : 0), c = nbk * 8 + 2 * t + (q & 1);
+        if (k < B2 && c < PW) S[k * PW + c] = make_float2(acc[0][nbk][q], acc[1][nbk][q]);
+      }
+    // warp 2: Kr*Cr, Kr*Ci ; warp 3: Ki*Cr, Ki*Ci  (Ci holds -Im(by))
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kx = g + ((q & 2) ? 8 : 0), ky = 2 * t + (q & 1);
+        cs[(((wid - 2) * 2 + h) * 16 + kx) * 8 + ky] = cacc[h][q];
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x < B2 * B2) {
+    const int kx = threadIdx.x % B2, ky = threadIdx.x / B2;
+    const float rr = cs[((0 * 2 + 0) * 16 + kx) * 8 + ky];  // Re(A) Re(conj by)
+    const float ri = cs[((0 * 2 + 1) * 16 + kx) * 8 + ky];  // Re(A) Im(conj by)
+    const float ir = cs[((1 * 2 + 0) * 16 + kx) * 8 + ky];  // Im(A) Re(conj by)
+    const float ii = cs[((1 * 2 + 1) * 16 + kx) * 8 + ky];  // Im(A) Im(conj by)
+    out[PW * PW + 2 * B2 * PW + kx + B2 * ky] = make_float2(rr - ii, ri + ir);
+  }
+}
+
 template <typename R>
 gs_status set_smem_attr(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -311,6 +534,17 @@ template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st) {
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
+  if (sizeof(R) == 4 && D.m == 4 && b2 == 8 && tile == 16 && !std::getenv("GS_NO_TC")) {
+    const size_t sh = (size_t)(4 * tc::SBT * tc::LD32 + 8 * tc::SBT * tc::LD16) * sizeof(float);
+    gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc, sh);
+    if (e != GS_OK) return e;
+    GS_LAUNCH("spread2d<f32>", st,
+              k_spread2d_tc<<<P->nwork, 128, sh, st>>>(P->work, P->fl, (const float*)D.win, (const float2*)D.w,
+                                                       (const float2*)D.bf, (const float2*)u, perm, P->M, P->nbx,
+                                                       (float2*)part, D.part_stride));
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  }
   return dispatch_wb(2 * D.m, b2, [&](auto wc, auto bc) -> gs_status {
     constexpr int W = decltype(wc)::value;
     constexpr int B2 = decltype(bc)::value;
