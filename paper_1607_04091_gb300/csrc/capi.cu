@@ -94,7 +94,7 @@ static void free_prec_d(PrecData<double>& D) {
 }
 
 static void free_plan(Plan* P) {
-  void* ps[] = {P->perm, P->fl, P->xi_sorted, P->bin_start, P->work, P->work_start, P->wcol, P->wcol_start,
+  void* ps[] = {P->perm, P->fl, P->xi_sorted, P->bin_start, P->work, P->work_start, P->work_order, P->wcol, P->wcol_start,
                 P->red, P->scal, P->flag, P->y64, P->r64, P->x64};
   for (void* p : ps)
     if (p) cudaFree(p);

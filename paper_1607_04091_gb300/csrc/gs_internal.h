@@ -117,6 +117,7 @@ struct Plan {
   int32_t* bin_start = nullptr;  // [nbins + 1] sample range of each bin
   int32_t* work = nullptr;       // [nwork][3] (bin, s0, s1)
   int32_t* work_start = nullptr; // [nbins + 1] work items of each bin
+  int32_t* work_order = nullptr; // [nwork] item indices, most samples first (launch order)
   int32_t* wcol = nullptr;       // work items grouped by bin column (bx), then row
   int32_t* wcol_start = nullptr; // [nbx + 1] offsets into wcol
   int nwork = 0;

@@ -42,7 +42,7 @@ __device__ inline int bcol(int k, int b, int N) { return (k < b) ? k : N - 1 - (
 //   y = wx wy v_int + wy sum_k bx_k v_xside_k + wx sum_k by_k v_yside_k + sum bx by X
 template <typename R, int W, int B2>
 __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
-    const int32_t* __restrict__ work, const int32_t* __restrict__ fl, const R* __restrict__ frac,
+    const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl, const R* __restrict__ frac,
     const R* __restrict__ win, const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b_rt,
     const C<R>* __restrict__ grid, const C<R>* __restrict__ hbuf, const C<R>* __restrict__ side, int n, R beta,
     const C<R>* __restrict__ x, int N, int64_t M, int nbx, int tile, const int32_t* __restrict__ perm,
@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
   C<R>* S0 = G + PW * PW;   // x-side k along y
   C<R>* S1 = S0 + b2 * PW;  // y-side k along x
   C<R>* XC = S1 + b2 * PW;  // corner coefficients [ky][kx]
-  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int it = order[blockIdx.x];  // work item (larger items launch first)
+  const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
   const int ox = (bin % nbx) * tile, oy = (bin / nbx) * tile;
   const int gx0 = ox - m + 1, gy0 = oy - m + 1;
   for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
 // lane.  No atomics: each address is written by one lane of one warp per step.
 template <typename R, int W, int B2>
 __global__ void __launch_bounds__(256) k_spread2d(
-    const int32_t* __restrict__ work, const int32_t* __restrict__ fl, const R* __restrict__ frac,
+    const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl, const R* __restrict__ frac,
     const R* __restrict__ win, const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b_rt,
     const C<R>* __restrict__ u, const int32_t* __restrict__ perm, int64_t M, int nbx, int tile, R beta, int batch,
     C<R>* __restrict__ part, int64_t stride) {
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(256) k_spread2d(
     cka[q] = (ch < b2 * b2) ? 3 + ch % b2 : 0;       // A[kx]
     ckb[q] = (ch < b2 * b2) ? 3 + b2 + ch / b2 : 0;  // conj(by[ky])
   }
-  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int it = order[blockIdx.x];  // work item (larger items launch first)
+  const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
   const int ox = (bin % nbx) * tile, oy = (bin / nbx) * tile;
   for (int sb = s0; sb < s1; sb += batch) {
     const int nb = min(batch, s1 - sb);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(256) k_spread2d(
   for (int q = 0; q < NCQ; ++q)
     if (lane + 32 * q < b2 * b2) CS[wid * b2 * b2 + lane + 32 * q] = cc[q];
   __syncthreads();
-  C<R>* out = part + blockIdx.x * stride;
+  C<R>* out = part + it * stride;
   for (int i = threadIdx.x; i < wsz; i += blockDim.x) {
     C<R> acc = mk<R>(0, 0);
     for (int q = 0; q < nw; ++q) acc = cadd(acc, base[(int64_t)q * wsz + i]);
@@ -267,24 +269,53 @@ __global__ void __launch_bounds__(256) k_spread2d(
 //   S0[k][y]  += v0_s[k] wy_s[y - py_s]                    x-sides,  v0 = u conj(bx_k) conj(wy)
 //   S1[k][x]  += v1_s[k] wx_s[x - px_s]                    y-sides,  v1 = u conj(wx) conj(by_k)
 //   Cc[kx][ky]+= A_s[kx] conj(by_s[ky])                     corners,  A = u conj(bx)
-// i.e. GEMMs with K = samples.  Phase 1 (thread per sample) writes a batch of 32
-// samples as dense operand rows in shared memory; phase 2 accumulates the output
-// tiles in registers with mma.sync m16n8k8 TF32 using the 3xTF32 split
-// (a_hi b_hi + a_hi b_lo + a_lo b_hi, float32-level accuracy).  Output: the same
-// partial-tile layout as k_spread2d.
+// i.e. GEMMs with K = samples.  The samples go in batches of 32:
+//   staging  cp.async copies the batch's per-sample inputs (taps, boundary
+//            factors, phases, u, grid indices) to shared memory while the
+//            previous batch is multiplied;
+//   phase 1  warp q writes operand q (v wx re, v wx im, wx, wy as rows of 32
+//            grid offsets, zero outside the sample's 8 taps) and two boundary
+//            operands, one lane per sample;
+//   phase 2  mma.sync m16n8k8 TF32 with the 3xTF32 split (a_hi b_hi + a_hi b_lo +
+//            a_lo b_hi, float32-level accuracy): warps 0-1 one 16-row block of
+//            the interior each (real and imaginary part share the wy fragments),
+//            warp 2 the x-sides and warp 3 the y-sides, both taken transposed
+//            (rows = grid offset, columns = k), and one half each of the corners.
+// Output: the same partial-tile layout as k_spread2d, written through shared
+// memory with 16-byte stores.
 namespace tc {
-constexpr int SBT = 32;         // samples per batch (the K of one round)
-constexpr int LD32 = 40;        // row stride of 32-wide operands (bank-conflict free fragments)
-constexpr int LD16 = 24;        // row stride of 16- and 8-wide operands
+constexpr int SBT = 32;  // samples per batch (the K of one round)
+constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
+constexpr int LDO = 40;  // rows of the 32-wide operands (conflict-free fragments)
+constexpr int LDV = 8;   // rows of the 8-wide boundary operands
+constexpr int LDK = 24;  // rows of the 16-wide corner operand (Re A | Im A)
+constexpr int LDS = 20;  // staged rows of 16 floats (conflict-free float4 reads)
+// operand area (floats)
+constexpr int O_AR = 0, O_AI = O_AR + SBT * LDO, O_BX = O_AI + SBT * LDO, O_BY = O_BX + SBT * LDO;
+constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + SBT * LDV, O_V1R = O_V0I + SBT * LDV;
+constexpr int O_V1I = O_V1R + SBT * LDV, O_CR = O_V1I + SBT * LDV, O_CI = O_CR + SBT * LDV;
+constexpr int O_K = O_CI + SBT * LDV;
+constexpr int N_OPER = O_K + SBT * LDK;
+// staging area (floats, after the operands)
+constexpr int S_WIN = N_OPER, S_BX = S_WIN + SBT * LDS, S_BY = S_BX + SBT * LDS;
+constexpr int S_W = S_BY + SBT * LDS;  // [j][4]: wx re, im, wy re, im
+constexpr int S_U = S_W + 4 * SBT;     // [j][2]
+constexpr int S_FL = S_U + 2 * SBT;    // [j][2] int
+constexpr int N_SMEM = S_FL + 2 * SBT;
+// partial tile (float2) and corner exchange, reusing the operand area at the end
+constexpr int PART = PW * PW + 2 * B2 * PW + B2 * B2;
+constexpr int O_CS = 2 * PART;  // [2 warps][16][8] floats
+static_assert(O_CS + 2 * 16 * 8 <= N_OPER, "epilogue must fit the operand area");
+static_assert(PART % 2 == 0, "partial tile copied as float4");
 
-__device__ inline uint32_t tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// x = hi + lo with hi = x rounded to the 10 explicit mantissa bits of TF32 (add half
+// an ulp of TF32 to the bit pattern, then clear the 13 low bits: round to nearest,
+// ties away from zero) and lo = x - hi exact in float32, |lo| <= 2^-11 |x|.  lo goes
+// to the tensor core as it is; TF32 uses its 10 leading mantissa bits, so the
+// split keeps about 21 bits of x.
 __device__ inline void split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32(x);
-  lo = tf32(x - __uint_as_float(hi));
+  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ inline void mma(float* c, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -313,173 +344,220 @@ __device__ inline void load_b(const float* B, int ld, int n0, int k0, int lane, 
   split(B[(k0 + t) * ld + n0 + g], hi[0], lo[0]);
   split(B[(k0 + t + 4) * ld + n0 + g], hi[1], lo[1]);
 }
+__device__ inline void cp_async16(float* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+__device__ inline void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+__device__ inline void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src));
+}
+__device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ inline void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Copies the inputs of samples sb .. sb+nb-1 to the staging area: warp 0 the 16
+// taps (4 x 16 B), warp 1 the 8 x-boundary factors, warp 2 the 8 y-boundary
+// factors (4 x 16 B each), warp 3 the two phases, u and the two grid indices.
+__device__ inline void stage(float* sm, int wid, int lane, int sb, int nb, const float* __restrict__ win,
+                             const float2* __restrict__ w, const float2* __restrict__ bf,
+                             const float2* __restrict__ u, const int32_t* __restrict__ perm,
+                             const int32_t* __restrict__ fl, int64_t M) {
+  if (lane >= nb) return;
+  const int64_t s = sb + lane;
+  if (wid == 0) {
+    const float* src = win + s * (2 * W);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cp_async16(sm + S_WIN + lane * LDS + 4 * c, src + 4 * c);
+  } else if (wid < 3) {
+    const float2* src = bf + (s + (wid == 2 ? M : 0)) * B2;
+    float* dst = sm + (wid == 1 ? S_BX : S_BY) + lane * LDS;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cp_async16(dst + 4 * c, src + 2 * c);
+  } else {
+    cp_async8(sm + S_W + 4 * lane, w + s);
+    cp_async8(sm + S_W + 4 * lane + 2, w + M + s);
+    cp_async8(sm + S_U + 2 * lane, u + (perm ? perm[s] : s));
+    cp_async4(sm + S_FL + 2 * lane, fl + s);
+    cp_async4(sm + S_FL + 2 * lane + 1, fl + M + s);
+  }
+}
 }  // namespace tc
 
-static __global__ void __launch_bounds__(128) k_spread2d_tc(
-    const int32_t* __restrict__ work, const int32_t* __restrict__ fl, const float* __restrict__ win,
+static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
+    const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl, const float* __restrict__ win,
     const float2* __restrict__ w, const float2* __restrict__ bf, const float2* __restrict__ u,
     const int32_t* __restrict__ perm, int64_t M, int nbx, float2* __restrict__ part, int64_t stride) {
   using namespace tc;
-  constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
   extern __shared__ __align__(16) float sm[];
-  float* Ar = sm;                    // [SBT][LD32]  (v wx) real part, rows x = px + a
-  float* Ai = Ar + SBT * LD32;       // imaginary part
-  float* By = Ai + SBT * LD32;       // wy at columns y = py + c
-  float* Bx = By + SBT * LD32;       // wx at columns x = px + a
-  float* V0r = Bx + SBT * LD32;      // [SBT][LD16] x-side coefficients
-  float* V0i = V0r + SBT * LD16;
-  float* V1r = V0i + SBT * LD16;     // y-side coefficients
-  float* V1i = V1r + SBT * LD16;
-  float* Kr = V1i + SBT * LD16;      // A = u conj(bx)
-  float* Ki = Kr + SBT * LD16;
-  float* Cr = Ki + SBT * LD16;       // conj(by)
-  float* Ci = Cr + SBT * LD16;
-  constexpr int NST = 4 * SBT * LD32 + 8 * SBT * LD16;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bin = work[3 * blockIdx.x], s0 = work[3 * blockIdx.x + 1], s1 = work[3 * blockIdx.x + 2];
+  const int it = order[blockIdx.x];  // work item (larger items launch first)
+  const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
   const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
-  // accumulators: [re/im or second product][n-block 0..3][4]
-  float acc[2][4][4];
-  float cacc[2][4];
+  stage(sm, wid, lane, s0, min(SBT, s1 - s0), win, w, bf, u, perm, fl, M);
+  cp_commit();
+  for (int i = threadIdx.x; i < N_OPER; i += blockDim.x) sm[i] = 0.0f;
+  // accumulators.  Warps 0-1: interior rows m0..m0+15, [re: 0-2 | im: 3-5][n-block].
+  // Warps 2-3: side product (2 = x-sides S0, 3 = y-sides S1) [2 m-blocks][re | im] in
+  // 0-3 and half of the corner product in 4.
+  float acc[6][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-      if (j < 2)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cacc[j][q] = 0.0f;
-    }
-  // operands start at zero; afterwards each thread clears only the windows it wrote
-  for (int i = threadIdx.x; i < NST; i += blockDim.x) sm[i] = 0.0f;
-  int prev_px = -1, prev_py = -1;
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0f;
+  const int m0 = (wid & 1) * 16;
+  const float* Aside = sm + (wid == 2 ? O_BY : O_BX);  // side A (transposed): wy for S0, wx for S1
+  const float* Bs0 = sm + (wid == 2 ? O_V0R : O_V1R);
+  const float* Bs1 = sm + (wid == 2 ? O_V0I : O_V1I);
+  const float* Bc = sm + (wid == 2 ? O_CR : O_CI);
+  // phase-1 role: the 32-wide operand this warp owns and where its last window sat
+  float* Own = sm + (wid == 0 ? O_AR : wid == 1 ? O_AI : wid == 2 ? O_BX : O_BY);
+  int prev = -1;
   for (int sb = s0; sb < s1; sb += SBT) {
     const int nb = min(SBT, s1 - sb);
-    if (threadIdx.x < SBT && prev_px >= 0) {
-      const int j = threadIdx.x;
+    cp_wait_all();
+    __syncthreads();  // staging of this batch visible; phase 2 of the last batch done
+    {
+      const int j = lane;
+      float* row = Own + j * LDO;
+      if (prev >= 0) {
 #pragma unroll
-      for (int a = 0; a < W; ++a) {
-        Ar[j * LD32 + prev_px + a] = 0.0f;
-        Ai[j * LD32 + prev_px + a] = 0.0f;
-        Bx[j * LD32 + prev_px + a] = 0.0f;
-        By[j * LD32 + prev_py + a] = 0.0f;
+        for (int a = 0; a < W; ++a) row[prev + a] = 0.0f;
+        prev = -1;
       }
-      if (j >= nb) {  // no sample in this slot now: clear its boundary rows too
+      if (j < nb) {
+        const float4 ww = *reinterpret_cast<const float4*>(sm + S_W + 4 * j);
+        const float2 wxs = make_float2(ww.x, ww.y), wys = make_float2(ww.z, ww.w);
+        const float2 us = *reinterpret_cast<const float2*>(sm + S_U + 2 * j);
+        const int* flj = reinterpret_cast<const int*>(sm + S_FL + 2 * j);
+        const int pos = (wid == 3) ? flj[1] - oy + 1 : flj[0] - ox + 1;
+        const float* tp = sm + S_WIN + j * LDS + (wid == 3 ? W : 0);
+        const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
+        const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        float scale = 1.0f;
+        if (wid < 2) {
+          const float2 vi = cmulc(cmulc(us, wxs), wys);
+          scale = (wid == 0) ? vi.x : vi.y;
+        }
+#pragma unroll
+        for (int a = 0; a < W; ++a) row[pos + a] = scale * tap[a];
+        prev = pos;
+        // boundary operands: warp 0 V0 (x-sides), 1 V1 (y-sides), 2 A = u conj(bx), 3 conj(by)
+        const float* bp = sm + ((wid == 0 || wid == 2) ? S_BX : S_BY) + j * LDS;
+        const float2 uwx = cmulc(us, wxs);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float4 f = *reinterpret_cast<const float4*>(bp + 4 * h);
+          const float2 bk[2] = {make_float2(f.x, f.y), make_float2(f.z, f.w)};
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * h + e;
+            if (wid == 0) {
+              const float2 v0 = cmulc(cmulc(us, bk[e]), wys);
+              sm[O_V0R + j * LDV + k] = v0.x;
+              sm[O_V0I + j * LDV + k] = v0.y;
+            } else if (wid == 1) {
+              const float2 v1 = cmulc(uwx, bk[e]);
+              sm[O_V1R + j * LDV + k] = v1.x;
+              sm[O_V1I + j * LDV + k] = v1.y;
+            } else if (wid == 2) {
+              const float2 ak = cmulc(us, bk[e]);
+              sm[O_K + j * LDK + k] = ak.x;
+              sm[O_K + j * LDK + B2 + k] = ak.y;
+            } else {
+              sm[O_CR + j * LDV + k] = bk[e].x;
+              sm[O_CI + j * LDV + k] = -bk[e].y;
+            }
+          }
+        }
+      } else {  // empty slot: its boundary rows are zero
 #pragma unroll
         for (int k = 0; k < B2; ++k) {
-          V0r[j * LD16 + k] = V0i[j * LD16 + k] = V1r[j * LD16 + k] = V1i[j * LD16 + k] = 0.0f;
-          Kr[j * LD16 + k] = Ki[j * LD16 + k] = Cr[j * LD16 + k] = Ci[j * LD16 + k] = 0.0f;
+          if (wid == 0) sm[O_V0R + j * LDV + k] = sm[O_V0I + j * LDV + k] = 0.0f;
+          else if (wid == 1) sm[O_V1R + j * LDV + k] = sm[O_V1I + j * LDV + k] = 0.0f;
+          else if (wid == 2) sm[O_K + j * LDK + k] = sm[O_K + j * LDK + B2 + k] = 0.0f;
+          else sm[O_CR + j * LDV + k] = sm[O_CI + j * LDV + k] = 0.0f;
         }
       }
-      prev_px = -1;
     }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      const int j = threadIdx.x, s = sb + j;
-      const float2 us = u[perm ? perm[s] : s];
-      const int px = fl[s] - ox + 1, py = fl[M + s] - oy + 1;
-      const float* wxp = win + ((int64_t)s * 2) * W;
-      const float* wyp = wxp + W;
-      const float2 wxs = w[s], wys = w[M + s];
-      const float2 vi = cmulc(cmulc(us, wxs), wys);
-      const float2 uwx = cmulc(us, wxs);
-      prev_px = px;
-      prev_py = py;
+    __syncthreads();  // operands complete; staging free
+    if (sb + SBT < s1) stage(sm, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, u, perm, fl, M);
+    cp_commit();
+    if (wid < 2) {
 #pragma unroll
-      for (int a = 0; a < W; ++a) {
-        const float wa = __ldg(wxp + a), wc = __ldg(wyp + a);
-        Ar[j * LD32 + px + a] = vi.x * wa;
-        Ai[j * LD32 + px + a] = vi.y * wa;
-        Bx[j * LD32 + px + a] = wa;
-        By[j * LD32 + py + a] = wc;
+      for (int k0 = 0; k0 < SBT; k0 += 8) {
+        uint32_t rh[4], rl[4], ih[4], il[4], bh[2], bl[2];
+        load_a(sm + O_AR, LDO, m0, k0, lane, rh, rl);
+        load_a(sm + O_AI, LDO, m0, k0, lane, ih, il);
+#pragma unroll
+        for (int nbk = 0; nbk < 3; ++nbk) {
+          load_b(sm + O_BY, LDO, nbk * 8, k0, lane, bh, bl);
+          mma3(acc[nbk], rh, rl, bh, bl);
+          mma3(acc[3 + nbk], ih, il, bh, bl);
+        }
       }
+    } else {
 #pragma unroll
-      for (int k = 0; k < B2; ++k) {
-        const float2 bxk = bf[(int64_t)s * B2 + k], byk = bf[(M + s) * B2 + k];
-        const float2 ak = cmulc(us, bxk);
-        const float2 v0 = cmulc(ak, wys);
-        const float2 v1 = cmulc(uwx, byk);
-        V0r[j * LD16 + k] = v0.x;
-        V0i[j * LD16 + k] = v0.y;
-        V1r[j * LD16 + k] = v1.x;
-        V1i[j * LD16 + k] = v1.y;
-        Kr[j * LD16 + k] = ak.x;
-        Ki[j * LD16 + k] = ak.y;
-        Cr[j * LD16 + k] = byk.x;
-        Ci[j * LD16 + k] = -byk.y;
+      for (int k0 = 0; k0 < SBT; k0 += 8) {
+        uint32_t ah[4], al[4], b0h[2], b0l[2], b1h[2], b1l[2];
+        load_b(Bs0, LDV, 0, k0, lane, b0h, b0l);
+        load_b(Bs1, LDV, 0, k0, lane, b1h, b1l);
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) {
+          load_a(Aside, LDO, 16 * mb, k0, lane, ah, al);
+          mma3(acc[2 * mb], ah, al, b0h, b0l);
+          mma3(acc[2 * mb + 1], ah, al, b1h, b1l);
+        }
+        load_a(sm + O_K, LDK, 0, k0, lane, ah, al);
+        load_b(Bc, LDV, 0, k0, lane, b0h, b0l);
+        mma3(acc[4], ah, al, b0h, b0l);
       }
     }
-    __syncthreads();
-    // phase 2: warp 0/1 interior rows 0-15 / 16-31; warp 2 x-sides (+ corners with A = Kr);
-    // warp 3 y-sides (+ corners with A = Ki)
-    const float* A0 = (wid < 2) ? Ar : (wid == 2 ? V0r : V1r);
-    const float* A1 = (wid < 2) ? Ai : (wid == 2 ? V0i : V1i);
-    const int lda = (wid < 2) ? LD32 : LD16;
-    const int m0 = (wid == 1) ? 16 : 0;
-    const float* Bm = (wid == 3) ? Bx : By;
-    const float* Ka = (wid == 2) ? Kr : Ki;
-    for (int k0 = 0; k0 < SBT; k0 += 8) {
-      uint32_t a0h[4], a0l[4], a1h[4], a1l[4];
-      load_a(A0, lda, m0, k0, lane, a0h, a0l);
-      load_a(A1, lda, m0, k0, lane, a1h, a1l);
-#pragma unroll
-      for (int nbk = 0; nbk < 4; ++nbk) {
-        uint32_t bh[2], bl[2];
-        load_b(Bm, LD32, nbk * 8, k0, lane, bh, bl);
-        mma3(acc[0][nbk], a0h, a0l, bh, bl);
-        mma3(acc[1][nbk], a1h, a1l, bh, bl);
-      }
-      if (wid >= 2) {
-        uint32_t kh[4], kl[4], ch[2], cl[2];
-        load_a(Ka, LD16, 0, k0, lane, kh, kl);
-        load_b(Cr, LD16, 0, k0, lane, ch, cl);
-        mma3(cacc[0], kh, kl, ch, cl);
-        load_b(Ci, LD16, 0, k0, lane, ch, cl);
-        mma3(cacc[1], kh, kl, ch, cl);
-      }
-    }
-    __syncthreads();
   }
-  // write the partial tile: P | S0 | S1 | corners
+  cp_wait_all();
+  __syncthreads();  // operands no longer read: the area holds the partial tile now
+  float* T = sm;    // float2 [PART] as floats
   const int g = lane >> 2, t = lane & 3;
-  float2* out = part + blockIdx.x * stride;
-  float* cs = sm;  // corner products exchanged between warps 2 and 3: [2 warps][2][16][8]
-  if (wid < 2) {
 #pragma unroll
-    for (int nbk = 0; nbk < 4; ++nbk)
+  for (int q = 0; q < 4; ++q) {
+    const int r = g + ((q & 2) ? 8 : 0), c = 2 * t + (q & 1);
+    if (wid < 2) {  // interior: rows x, columns y
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int x = (wid == 1 ? 16 : 0) + g + ((q & 2) ? 8 : 0), y = nbk * 8 + 2 * t + (q & 1);
-        if (x < PW && y < PW) out[x * PW + y] = make_float2(acc[0][nbk][q], acc[1][nbk][q]);
-      }
-  } else {
-    float2* S = out + PW * PW + (wid == 3 ? B2 * PW : 0);
+      for (int nbk = 0; nbk < 3; ++nbk)
+        if (m0 + r < PW) {
+          const int o = (m0 + r) * PW + nbk * 8 + c;
+          T[2 * o] = acc[nbk][q];
+          T[2 * o + 1] = acc[3 + nbk][q];
+        }
+    } else {  // sides: rows are the grid offset (y for S0, x for S1), columns k
 #pragma unroll
-    for (int nbk = 0; nbk < 4; ++nbk)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = g + ((q & 2) ? 8 : 0), c = nbk * 8 + 2 * t + (q & 1);
-        if (k < B2 && c < PW) S[k * PW + c] = make_float2(acc[0][nbk][q], acc[1][nbk][q]);
-      }
-    // warp 2: Kr*Cr, Kr*Ci ; warp 3: Ki*Cr, Ki*Ci  (Ci holds -Im(by))
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int kx = g + ((q & 2) ? 8 : 0), ky = 2 * t + (q & 1);
-        cs[(((wid - 2) * 2 + h) * 16 + kx) * 8 + ky] = cacc[h][q];
-      }
+      for (int mb = 0; mb < 2; ++mb)
+        if (16 * mb + r < PW) {
+          const int o = PW * PW + (wid == 3 ? B2 * PW : 0) + c * PW + 16 * mb + r;
+          T[2 * o] = acc[2 * mb][q];
+          T[2 * o + 1] = acc[2 * mb + 1][q];
+        }
+      sm[O_CS + ((wid - 2) * 16 + r) * 8 + c] = acc[4][q];
+    }
   }
   __syncthreads();
   if (threadIdx.x < B2 * B2) {
     const int kx = threadIdx.x % B2, ky = threadIdx.x / B2;
-    const float rr = cs[((0 * 2 + 0) * 16 + kx) * 8 + ky];  // Re(A) Re(conj by)
-    const float ri = cs[((0 * 2 + 1) * 16 + kx) * 8 + ky];  // Re(A) Im(conj by)
-    const float ir = cs[((1 * 2 + 0) * 16 + kx) * 8 + ky];  // Im(A) Re(conj by)
-    const float ii = cs[((1 * 2 + 1) * 16 + kx) * 8 + ky];  // Im(A) Im(conj by)
-    out[PW * PW + 2 * B2 * PW + kx + B2 * ky] = make_float2(rr - ii, ri + ir);
+    const float rr = sm[O_CS + (0 * 16 + kx) * 8 + ky];       // Re(A) Re(conj by)
+    const float ir = sm[O_CS + (0 * 16 + 8 + kx) * 8 + ky];   // Im(A) Re(conj by)
+    const float ri = sm[O_CS + (1 * 16 + kx) * 8 + ky];       // Re(A) Im(conj by)
+    const float ii = sm[O_CS + (1 * 16 + 8 + kx) * 8 + ky];   // Im(A) Im(conj by)
+    const int o = PW * PW + 2 * B2 * PW + kx + B2 * ky;
+    T[2 * o] = rr - ii;
+    T[2 * o + 1] = ri + ir;
   }
+  __syncthreads();
+  float4* out = reinterpret_cast<float4*>(part + it * stride);
+  const float4* src = reinterpret_cast<const float4*>(T);
+  for (int i = threadIdx.x; i < PART / 2; i += blockDim.x) out[i] = src[i];
 }
 
 template <typename R>
@@ -522,7 +600,7 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
     gs_status e = set_smem_attr<R>((const void*)k_interp2d<R, W, B2>, sh);
     if (e != GS_OK) return e;
     GS_LAUNCH(pname<R>("interp2d<f32>", "interp2d<f64>"), st,
-              k_interp2d<R, W, B2><<<P->nwork, 128, sh, st>>>(P->work, P->fl, D.frac, D.win, D.w, D.bf, b, D.grid,
+              k_interp2d<R, W, B2><<<P->nwork, 128, sh, st>>>(P->work, P->work_order, P->fl, D.frac, D.win, D.w, D.bf, b, D.grid,
                                                               D.hbuf, D.side, (int)P->n, (R)D.beta, x, (int)P->N,
                                                               P->M, P->nbx, tile, perm, y));
     GS_CUDA(cudaGetLastError());
@@ -534,12 +612,12 @@ template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st) {
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
-  if (sizeof(R) == 4 && D.m == 4 && b2 == 8 && tile == 16 && !std::getenv("GS_NO_TC")) {
-    const size_t sh = (size_t)(4 * tc::SBT * tc::LD32 + 8 * tc::SBT * tc::LD16) * sizeof(float);
+  if (sizeof(R) == 4 && D.m == 4 && b2 == 8 && tile == 16 && D.part_stride == tc::PART && !std::getenv("GS_NO_TC")) {
+    const size_t sh = (size_t)tc::N_SMEM * sizeof(float);
     gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc, sh);
     if (e != GS_OK) return e;
     GS_LAUNCH("spread2d<f32>", st,
-              k_spread2d_tc<<<P->nwork, 128, sh, st>>>(P->work, P->fl, (const float*)D.win, (const float2*)D.w,
+              k_spread2d_tc<<<P->nwork, 128, sh, st>>>(P->work, P->work_order, P->fl, (const float*)D.win, (const float2*)D.w,
                                                        (const float2*)D.bf, (const float2*)u, perm, P->M, P->nbx,
                                                        (float2*)part, D.part_stride));
     GS_CUDA(cudaGetLastError());
@@ -557,7 +635,7 @@ gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t*
     gs_status e = set_smem_attr<R>((const void*)k_spread2d<R, W, B2>, sh);
     if (e != GS_OK) return e;
     GS_LAUNCH(pname<R>("spread2d<f32>", "spread2d<f64>"), st,
-              k_spread2d<R, W, B2><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.win, D.w, D.bf, b, u,
+              k_spread2d<R, W, B2><<<P->nwork, warps * 32, sh, st>>>(P->work, P->work_order, P->fl, D.frac, D.win, D.w, D.bf, b, u,
                                                                      perm, P->M, P->nbx, tile, (R)D.beta, batch, part,
                                                                      D.part_stride));
     GS_CUDA(cudaGetLastError());

@@ -474,6 +474,16 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
     GS_CUDA(cudaMemcpyAsync(P->work, work.data(), work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   GS_CUDA(cudaMemcpyAsync(P->work_start, wstart.data(), wstart.size() * sizeof(int32_t),
                           cudaMemcpyHostToDevice, st));
+  // launch order: larger items first, so that the last wave holds the short ones
+  std::vector<int32_t> order(P->nwork);
+  for (int i = 0; i < P->nwork; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return work[3 * a + 2] - work[3 * a + 1] > work[3 * b + 2] - work[3 * b + 1];
+  });
+  GS_TRY(dalloc(&P->work_order, order.size()));
+  if (!order.empty())
+    GS_CUDA(cudaMemcpyAsync(P->work_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            st));
   // the same work items grouped by bin column (for reductions along x)
   std::vector<int32_t> wcol, wcs(P->nbx + 1);
   for (int bx = 0; bx < P->nbx; ++bx) {
