@@ -139,8 +139,11 @@ struct Plan {
 gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStream_t st);
 // implemented in nfft.cu / direct.cu.  perm != NULL: samples in the caller's
 // order (y[perm[s]]); perm == NULL: samples in the plan's sorted order.
+// norm_part != NULL (2D plans only): the interpolation also writes, per work
+// item i, the sum of |y_s|^2 over its samples to norm_part[i] (nwork values).
 template <typename R>
-gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st);
+gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
+                 double* norm_part = nullptr);
 template <typename R>
 gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st);
 template <typename R>
@@ -160,7 +163,8 @@ inline gs_status apply_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
 }
 // per-sample 2D kernels (persample2d_f32.cu / persample2d_f64.cu)
 template <typename R>
-gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st);
+gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
+                         double* norm_part = nullptr);
 template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st);
 template <typename R>

@@ -17,6 +17,8 @@
 //   hbuf  [j][lx]      N x n: x-transform of every coefficient row j (2D)
 //   side  [2][2b][n]   forward: x-side grids along y; adjoint: both side grids
 //   part  per spread work item: padded tile, side segments, corner sums
+// The grid size n = sigma 2^J and the bin count n / tile are powers of two, so
+// periodic indices wrap with the mask n - 1.
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>
@@ -70,7 +72,7 @@ __global__ void k_fwd1d_fft(const C<R>* __restrict__ x, const R* __restrict__ de
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     R dv = deap[i];
     if (dv != (R)0) {
-      int idx = (int)((i - N / 2 + n) % n);
+      int idx = (int)((i - N / 2) & (n - 1));
       buf[brev(idx, logn)] = cscale(x[i], dv);
     }
   }
@@ -183,7 +185,7 @@ __global__ void k_interp1d(const int32_t* __restrict__ fl, const R* __restrict__
   C<R> v = mk<R>(0, 0);
   for (int a = 0; a < 2 * m; ++a) {
     int l = f - m + 1 + a;
-    l = (l % n + n) % n;
+    l &= n - 1;
     R d = t + (R)(m - 1 - a);
     R wv = kb_window(d, m, beta);
     C<R> g = grid[l];
@@ -248,7 +250,7 @@ __global__ void k_reduce1d(const int32_t* __restrict__ work_start, const C<R>* _
   const int bx = gx / tile, PW = tile + 2 * m;
   int cand[3], nc = 0;
   for (int dx = -1; dx <= 1; ++dx) {
-    int nb = ((bx + dx) % nbx + nbx) % nbx;
+    int nb = (bx + dx) & (nbx - 1);
     bool dup = false;
     for (int q = 0; q < nc; ++q) dup |= (cand[q] == nb);
     if (!dup) cand[nc++] = nb;
@@ -256,7 +258,7 @@ __global__ void k_reduce1d(const int32_t* __restrict__ work_start, const C<R>* _
   C<R> acc = mk<R>(0, 0);
   for (int c = 0; c < nc; ++c) {
     int nb = cand[c];
-    int q0 = ((gx - nb * tile + m) % n + n) % n;
+    int q0 = (gx - nb * tile + m) & (n - 1);
     for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
       for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + q]);
   }
@@ -295,7 +297,7 @@ __global__ void k_adj1d_fft(const C<R>* __restrict__ grid, const R* __restrict__
     C<R> v;
     if (i < b) v = bsum[i];
     else if (i >= N - b) v = bsum[b + (N - 1 - i)];
-    else v = cscale(buf[(i - N / 2 + n) % n], deap[i]);
+    else v = cscale(buf[(i - N / 2) & (n - 1)], deap[i]);
     z[i] = v;
   }
 }
@@ -315,7 +317,7 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
     int r = t / N, i = t - r * N;
     R dv = deap[i];
     if (dv != (R)0) {
-      int idx = (i - N / 2 + n) % n;
+      int idx = (i - N / 2) & (n - 1);
       buf[r * n + brev(idx, logn)] = cscale(x[(int64_t)(j0 + r) * N + i], dv);
     }
   }
@@ -350,7 +352,7 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
       int i = (k < b) ? k : (N - 1 - (k - b));
       v = x[(int64_t)j * N + i];
     }
-    int idx = (j - N / 2 + n) % n;
+    int idx = (j - N / 2) & (n - 1);
     buf[c * n + brev(idx, logn)] = cscale(v, dv);
   }
   __syncthreads();
@@ -370,7 +372,7 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
 __device__ inline int neighbours(int bx, int nbx, int* cand) {
   int nc = 0;
   for (int dx = -1; dx <= 1; ++dx) {
-    int nb = ((bx + dx) % nbx + nbx) % nbx;
+    int nb = (bx + dx) & (nbx - 1);
     bool dup = false;
     for (int q = 0; q < nc; ++q) dup |= (cand[q] == nb);
     if (!dup) cand[nc++] = nb;
@@ -392,8 +394,9 @@ __global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<
   for (int iy = 0; iy < ncy; ++iy)
     for (int ix = 0; ix < ncx; ++ix) {
       int nb = cy[iy] * nbx + cx[ix];
-      int qx0 = ((gx - cx[ix] * tile + m) % n + n) % n;
-      int qy0 = ((gy - cy[iy] * tile + m) % n + n) % n;
+      int qx0 = (gx - cx[ix] * tile + m) & (n - 1);
+      int qy0 = (gy - cy[iy] * tile + m) & (n - 1);
+      if (qx0 >= PW || qy0 >= PW) continue;  // this bin's tiles do not reach (gx, gy)
       for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
         for (int qx = qx0; qx < PW; qx += n)
           for (int qy = qy0; qy < PW; qy += n) acc = cadd(acc, part[wi * stride + qx * PW + qy]);
@@ -420,7 +423,7 @@ __global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const in
   const int nc = neighbours(gb, nbx, cn);
   C<R> acc = mk<R>(0, 0);
   for (int ci = 0; ci < nc; ++ci) {
-    const int q0 = ((g - cn[ci] * tile + m) % n + n) % n;
+    const int q0 = (g - cn[ci] * tile + m) & (n - 1);
     const int r0 = (which == 0) ? work_start[cn[ci] * nbx] : wcol_start[cn[ci]];
     const int r1 = (which == 0) ? work_start[(cn[ci] + 1) * nbx] : wcol_start[cn[ci] + 1];
     for (int r = r0 + wl; r < r1; r += nl) {
@@ -461,7 +464,7 @@ __global__ void k_adj2d_pass2(const C<R>* __restrict__ grid, const C<R>* __restr
     R dv = deap[j];
     if (dv == (R)0) continue;
     int col = c0 + c;
-    C<R> v = cscale(buf[c * n + (j - N / 2 + n) % n], dv);
+    C<R> v = cscale(buf[c * n + ((j - N / 2) & (n - 1))], dv);
     if (col < n) {
       hbuf[(int64_t)j * n + col] = v;
     } else {
@@ -504,7 +507,7 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
     R dv = deap[i];
     C<R> v;
     if (dv != (R)0) {
-      v = cscale(buf[r * n + (i - N / 2 + n) % n], dv);
+      v = cscale(buf[r * n + ((i - N / 2) & (n - 1))], dv);
     } else {
       bool jb = (j < b) || (j >= N - b);
       if (!jb) continue;  // x-side entries come from pass 2
@@ -542,7 +545,8 @@ constexpr int FOUR_STEP_N = 4096;  // 1D grids from this size use the two-pass F
 
 // ---------------------------------------------------------------- host drivers
 template <typename R>
-gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st) {
+gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
+                 double* norm_part) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b;
   const int64_t M = P->M;
   const R beta = (R)D.beta;
@@ -578,7 +582,7 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
               k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
                                                                                 cols, D.tw, D.grid, D.side));
-    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st);
+    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part);
     if (si != GS_OK) return si;
   }
   GS_CUDA(cudaGetLastError());
@@ -749,8 +753,10 @@ gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t
   return GS_OK;
 }
 
-template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
-template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t);
+template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
+                                 double*);
+template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t,
+                                  double*);
 template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
 template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,
                                    cudaStream_t);

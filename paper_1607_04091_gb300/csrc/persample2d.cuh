@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
     const R* __restrict__ win, const C<R>* __restrict__ w, const C<R>* __restrict__ bf, int b_rt,
     const C<R>* __restrict__ grid, const C<R>* __restrict__ hbuf, const C<R>* __restrict__ side, int n, R beta,
     const C<R>* __restrict__ x, int N, int64_t M, int nbx, int tile, const int32_t* __restrict__ perm,
-    C<R>* __restrict__ y) {
+    C<R>* __restrict__ y, double* __restrict__ norm_part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int m = W / 2;
   const int b2 = (B2 >= 0) ? B2 : 2 * b_rt;
@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
     XC[t] = x[(int64_t)bcol(ky, b, N) * N + bcol(kx, b, N)];
   }
   __syncthreads();
+  double nacc = 0.0;
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
     const int px = fl[s] - ox, py = fl[M + s] - oy;
     R wx[W], wy[W];
@@ -130,6 +131,20 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
       out = cadd(out, cc);
     }
     y[perm ? perm[s] : s] = out;
+    nacc += (double)out.x * out.x + (double)out.y * out.y;
+  }
+  if (norm_part) {  // ||y||^2 over this item's samples: lanes, then warps, in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+    __syncthreads();  // the staged tile is no longer read
+    double* wsum = reinterpret_cast<double*>(smraw);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = nacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += wsum[i];
+      norm_part[it] = t;
+    }
   }
 }
 
@@ -588,7 +603,8 @@ gs_status dispatch_wb(int W, int B2, F&& f) {
 }  // namespace dev
 
 template <typename R>
-gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st) {
+gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
+                         double* norm_part) {
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
   if (P->nwork == 0) return GS_OK;
@@ -602,7 +618,7 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
     GS_LAUNCH(pname<R>("interp2d<f32>", "interp2d<f64>"), st,
               k_interp2d<R, W, B2><<<P->nwork, 128, sh, st>>>(P->work, P->work_order, P->fl, D.frac, D.win, D.w, D.bf, b, D.grid,
                                                               D.hbuf, D.side, (int)P->n, (R)D.beta, x, (int)P->N,
-                                                              P->M, P->nbx, tile, perm, y));
+                                                              P->M, P->nbx, tile, perm, y, norm_part));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   });

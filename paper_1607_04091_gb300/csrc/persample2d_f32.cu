@@ -2,6 +2,7 @@
 #include "persample2d.cuh"
 
 namespace gs {
-template gs_status launch_interp2d<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
+template gs_status launch_interp2d<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
+                                           double*);
 template gs_status launch_spread2d<float>(Plan*, PrecData<float>&, const float2*, const int32_t*, float2*, cudaStream_t);
 }  // namespace gs

@@ -68,31 +68,81 @@ __global__ void k_store(const double* part, int np, double* scal, int slot, cons
   if (threadIdx.x == 0) scal[slot] = s;
 }
 
-// alpha = gamma / ||q||^2
+// alpha = gamma / ||q||^2, gamma = ||s||^2 of the last iteration (S_GNEW, which
+// k_beta_p writes while its other blocks still read the previous S_GAMMA)
 __global__ void k_alpha(const double* part, int np, double* scal, int* flag) {
   if (flag[0] != F_RUN) return;
   double d = block_sum(part, np);
   if (threadIdx.x == 0) {
+    const double gam = scal[S_GNEW];
+    scal[S_GAMMA] = gam;
     scal[S_DELTA] = d;
-    double a = scal[S_GAMMA] / d;
+    double a = gam / d;
     if (!(d > 0.0) || !isfinite(a)) flag[0] = F_BREAK;
     else scal[S_ALPHA] = a;
   }
 }
 
-// gamma' = ||s||^2, beta = gamma'/gamma, stop test
-__global__ void k_beta(const double* part, int np, double* scal, int* flag) {
-  if (flag[0] != F_RUN) return;
-  double g = block_sum(part, np);
-  if (threadIdx.x == 0) {
-    double beta = g / scal[S_GAMMA];
+// gamma' = ||s||^2, beta = gamma'/gamma, stop test, and p = s + beta p, in one
+// grid: every block forms the same sum of the partials in the same order; block
+// 0 records the scalars and the stop flag.  The stop flag is read once per
+// block (it may change while the grid runs; a block that sees it set skips its
+// part of p, which the ending loop no longer reads).
+template <typename R>
+__global__ void k_beta_p(const double* __restrict__ part, int np, C<R>* __restrict__ p,
+                         const C<R>* __restrict__ s, int64_t n, double* scal, int* flag) {
+  __shared__ int run;
+  if (threadIdx.x == 0) run = (flag[0] == F_RUN);
+  __syncthreads();
+  if (!run) return;
+  const double g = block_sum(part, np);
+  const double beta = g / scal[S_GAMMA];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     scal[S_BETA] = beta;
-    scal[S_GAMMA] = g;
+    scal[S_GNEW] = g;
     scal[S_ITER] += 1.0;
     if (!isfinite(beta)) flag[0] = F_BREAK;
     else if (g <= scal[S_THR2]) flag[0] = F_CONV;
     else if (scal[S_ITER] >= scal[S_MAXIT]) flag[0] = F_MAXIT;
   }
+  if (!isfinite(beta)) return;
+  const R bt = (R)beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    C<R> v = p[i], sv = s[i];
+    v.x = sv.x + bt * v.x;
+    v.y = sv.y + bt * v.y;
+    p[i] = v;
+  }
+}
+
+// x += alpha p and s -= alpha z (both ncoef), with the partial sums of the new
+// ||s||^2 per block (fixed order: threads, then a tree over the block)
+template <typename R>
+__global__ void k_update_xs(C<R>* __restrict__ x, const C<R>* __restrict__ p, C<R>* __restrict__ s,
+                            const C<R>* __restrict__ z, int64_t n, const double* scal, const int* flag,
+                            double* __restrict__ part) {
+  __shared__ double sh[256];
+  if (flag[0] != F_RUN) return;
+  const R a = (R)scal[S_ALPHA];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    C<R> v = x[i], pv = p[i];
+    v.x += a * pv.x;
+    v.y += a * pv.y;
+    x[i] = v;
+    C<R> sv = s[i], zv = z[i];
+    sv.x -= a * zv.x;
+    sv.y -= a * zv.y;
+    s[i] = sv;
+    acc += sqn(sv);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+    if (threadIdx.x < t) sh[threadIdx.x] += sh[threadIdx.x + t];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 // x += alpha p (ncoef) and r -= alpha q (M)
@@ -114,20 +164,6 @@ __global__ void k_update_xr(C<R>* __restrict__ x, const C<R>* __restrict__ p, in
       v.y -= a * qv.y;
       r[k] = v;
     }
-  }
-}
-
-// p = s + beta p
-template <typename R>
-__global__ void k_update_p(C<R>* __restrict__ p, const C<R>* __restrict__ s, int64_t n, const double* scal,
-                           const int* flag) {
-  if (flag[0] != F_RUN) return;
-  const R bt = (R)scal[S_BETA];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    C<R> v = p[i], sv = s[i];
-    v.x = sv.x + bt * v.x;
-    v.y = sv.y + bt * v.y;
-    p[i] = v;
   }
 }
 
@@ -153,6 +189,7 @@ __global__ void k_to32(float2* __restrict__ o, const double2* __restrict__ in, i
 // scalars for a new CGLS pass: gamma = ||s0||^2 (already in S_TMP), thresholds
 __global__ void k_init_pass(double* scal, int* flag, double thr2, double maxit) {
   scal[S_GAMMA] = scal[S_TMP];
+  scal[S_GNEW] = scal[S_TMP];
   scal[S_S0] = scal[S_TMP];
   scal[S_THR2] = thr2;
   scal[S_ITER] = 0.0;
@@ -194,26 +231,35 @@ __global__ void k_loop_enter(cudaGraphConditionalHandle h, const int* flag, cons
 template <typename R>
 gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st) {
   const int64_t nc = P->ncoef, M = P->M;
-  gs_status s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
-  if (s != GS_OK) return s;
-  GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
-  GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
+  // q = T p with ||q||^2 partials: per work item from the 2D interpolation, else a grid reduction
+  int np = RED_BLOCKS;
+  gs_status s;
+  if (!P->direct && P->dims == 2) {
+    np = P->nwork;
+    s = nfft_T<R>(P, D, D.vp, D.vq, nullptr, st, P->red);
+    if (s != GS_OK) return s;
+  } else {
+    s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
+    if (s != GS_OK) return s;
+    GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
+  }
+  GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, np, P->scal, P->flag));
+  // ||s||^2 partials go after the ||q||^2 ones
+  double* red_s = P->red + std::max<int64_t>(P->nwork, RED_BLOCKS);
+  const int gs = grid_for(nc);
   if (normal_eq) {
-    GS_LAUNCH("cgls_axpy", st,
-              k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(D.vx, D.vp, nc, nullptr, nullptr, 0, P->scal, P->flag));
     s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
     if (s != GS_OK) return s;
     GS_LAUNCH("cgls_axpy", st,
-              k_update_xr<R><<<grid_for(nc), 256, 0, st>>>(nullptr, nullptr, 0, D.vs, D.vz, nc, P->scal, P->flag));
+              k_update_xs<R><<<gs, 256, 0, st>>>(D.vx, D.vp, D.vs, D.vz, nc, P->scal, P->flag, red_s));
   } else {
     GS_LAUNCH("cgls_axpy", st,
               k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal, P->flag));
     s = apply_TH<R>(P, D, D.vr, D.vs, nullptr, st);
     if (s != GS_OK) return s;
+    GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<gs, 256, 0, st>>>(D.vs, nc, red_s, P->flag));
   }
-  GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vs, nc, P->red, P->flag));
-  GS_LAUNCH("cgls_scalar", st, k_beta<<<1, 256, 0, st>>>(P->red, RED_BLOCKS, P->scal, P->flag));
-  GS_LAUNCH("cgls_axpy", st, k_update_p<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc, P->scal, P->flag));
+  GS_LAUNCH("cgls_scalar", st, k_beta_p<R><<<gs, 256, 0, st>>>(red_s, gs, D.vp, D.vs, nc, P->scal, P->flag));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -417,6 +463,7 @@ __global__ void k_pass_init(double* scal, int* flag) {
   const double ns2 = scal[S_TMP];
   const double thr = fmax(0.25 * scal[G_THR2], scal[G_IRTOL2] * ns2);
   scal[S_GAMMA] = ns2;
+  scal[S_GNEW] = ns2;
   scal[S_S0] = ns2;
   scal[S_THR2] = thr;
   scal[S_ITER] = 0.0;

@@ -510,7 +510,8 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
   k_twiddle<<<(P->n / 2 + 255) / 256, 256, 0, st>>>(P->n, P->d.tw, P->f.tw);
   GS_CUDA(cudaGetLastError());
 
-  GS_TRY(dalloc(&P->red, (size_t)std::max(8192, P->nwork + 1024)));
+  // reduction partials: per work item (or 512 blocks), then up to 1184 blocks
+  GS_TRY(dalloc(&P->red, (size_t)std::max(8192, P->nwork + 2048)));
   GS_TRY(dalloc(&P->scal, 64));
   GS_TRY(dalloc(&P->flag, 16));
   GS_TRY(dalloc(&P->y64, (size_t)2 * M));
