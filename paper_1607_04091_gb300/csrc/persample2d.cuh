@@ -302,15 +302,15 @@ namespace tc {
 constexpr int SBT = 32;  // samples per batch (the K of one round)
 constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
 constexpr int LDO = 40;  // rows of the 32-wide operands (conflict-free fragments)
-constexpr int LDV = 8;   // rows of the 8-wide boundary operands
-constexpr int LDK = 24;  // rows of the 16-wide corner operand (Re A | Im A)
+constexpr int LDT = 36;  // boundary operands stored transposed, [k][sample]: conflict-free
+                         // writes (one lane per sample) and fragment loads
 constexpr int LDS = 20;  // staged rows of 16 floats (conflict-free float4 reads)
 // operand area (floats)
 constexpr int O_AR = 0, O_AI = O_AR + SBT * LDO, O_BX = O_AI + SBT * LDO, O_BY = O_BX + SBT * LDO;
-constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + SBT * LDV, O_V1R = O_V0I + SBT * LDV;
-constexpr int O_V1I = O_V1R + SBT * LDV, O_CR = O_V1I + SBT * LDV, O_CI = O_CR + SBT * LDV;
-constexpr int O_K = O_CI + SBT * LDV;
-constexpr int N_OPER = O_K + SBT * LDK;
+constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + B2 * LDT, O_V1R = O_V0I + B2 * LDT;
+constexpr int O_V1I = O_V1R + B2 * LDT, O_CR = O_V1I + B2 * LDT, O_CI = O_CR + B2 * LDT;
+constexpr int O_K = O_CI + B2 * LDT;  // [Re A_0..7 | Im A_0..7][sample]
+constexpr int N_OPER = O_K + 2 * B2 * LDT;
 // staging area (floats, after the operands)
 constexpr int S_WIN = N_OPER, S_BX = S_WIN + SBT * LDS, S_BY = S_BX + SBT * LDS;
 constexpr int S_W = S_BY + SBT * LDS;  // [j][4]: wx re, im, wy re, im
@@ -333,17 +333,11 @@ __device__ inline void split(float x, uint32_t& hi, uint32_t& lo) {
   lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ inline void mma(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-__device__ inline void mma3(float* c, const uint32_t* ah, const uint32_t* al, const uint32_t* bh,
-                            const uint32_t* bl) {
-  mma(c, ah, bh);
-  mma(c, ah, bl);
-  mma(c, al, bh);
 }
 // A fragment (16 x 8, rows m0.., k-columns k0..) from an operand stored [k][m]
 __device__ inline void load_a(const float* A, int ld, int m0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
@@ -358,6 +352,20 @@ __device__ inline void load_b(const float* B, int ld, int n0, int k0, int lane, 
   const int g = lane >> 2, t = lane & 3;
   split(B[(k0 + t) * ld + n0 + g], hi[0], lo[0]);
   split(B[(k0 + t + 4) * ld + n0 + g], hi[1], lo[1]);
+}
+// A fragment from an operand stored [m][k]
+__device__ inline void load_aT(const float* A, int ld, int m0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+  split(A[(m0 + g) * ld + k0 + t], hi[0], lo[0]);
+  split(A[(m0 + g + 8) * ld + k0 + t], hi[1], lo[1]);
+  split(A[(m0 + g) * ld + k0 + t + 4], hi[2], lo[2]);
+  split(A[(m0 + g + 8) * ld + k0 + t + 4], hi[3], lo[3]);
+}
+// B fragment from an operand stored [n][k]
+__device__ inline void load_bT(const float* B, int ld, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+  split(B[(n0 + g) * ld + k0 + t], hi[0], lo[0]);
+  split(B[(n0 + g) * ld + k0 + t + 4], hi[1], lo[1]);
 }
 __device__ inline void cp_async16(float* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -472,63 +480,71 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
             const int k = 2 * h + e;
             if (wid == 0) {
               const float2 v0 = cmulc(cmulc(us, bk[e]), wys);
-              sm[O_V0R + j * LDV + k] = v0.x;
-              sm[O_V0I + j * LDV + k] = v0.y;
+              sm[O_V0R + k * LDT + j] = v0.x;
+              sm[O_V0I + k * LDT + j] = v0.y;
             } else if (wid == 1) {
               const float2 v1 = cmulc(uwx, bk[e]);
-              sm[O_V1R + j * LDV + k] = v1.x;
-              sm[O_V1I + j * LDV + k] = v1.y;
+              sm[O_V1R + k * LDT + j] = v1.x;
+              sm[O_V1I + k * LDT + j] = v1.y;
             } else if (wid == 2) {
               const float2 ak = cmulc(us, bk[e]);
-              sm[O_K + j * LDK + k] = ak.x;
-              sm[O_K + j * LDK + B2 + k] = ak.y;
+              sm[O_K + k * LDT + j] = ak.x;
+              sm[O_K + (B2 + k) * LDT + j] = ak.y;
             } else {
-              sm[O_CR + j * LDV + k] = bk[e].x;
-              sm[O_CI + j * LDV + k] = -bk[e].y;
+              sm[O_CR + k * LDT + j] = bk[e].x;
+              sm[O_CI + k * LDT + j] = -bk[e].y;
             }
           }
         }
       } else {  // empty slot: its boundary rows are zero
 #pragma unroll
         for (int k = 0; k < B2; ++k) {
-          if (wid == 0) sm[O_V0R + j * LDV + k] = sm[O_V0I + j * LDV + k] = 0.0f;
-          else if (wid == 1) sm[O_V1R + j * LDV + k] = sm[O_V1I + j * LDV + k] = 0.0f;
-          else if (wid == 2) sm[O_K + j * LDK + k] = sm[O_K + j * LDK + B2 + k] = 0.0f;
-          else sm[O_CR + j * LDV + k] = sm[O_CI + j * LDV + k] = 0.0f;
+          if (wid == 0) sm[O_V0R + k * LDT + j] = sm[O_V0I + k * LDT + j] = 0.0f;
+          else if (wid == 1) sm[O_V1R + k * LDT + j] = sm[O_V1I + k * LDT + j] = 0.0f;
+          else if (wid == 2) sm[O_K + k * LDT + j] = sm[O_K + (B2 + k) * LDT + j] = 0.0f;
+          else sm[O_CR + k * LDT + j] = sm[O_CI + k * LDT + j] = 0.0f;
         }
       }
     }
     __syncthreads();  // operands complete; staging free
     if (sb + SBT < s1) stage(sm, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, u, perm, fl, M);
     cp_commit();
+    // The three products of the split go term by term over the warp's tiles, so
+    // that consecutive MMAs never update the same accumulator.
     if (wid < 2) {
 #pragma unroll
       for (int k0 = 0; k0 < SBT; k0 += 8) {
-        uint32_t rh[4], rl[4], ih[4], il[4], bh[2], bl[2];
-        load_a(sm + O_AR, LDO, m0, k0, lane, rh, rl);
-        load_a(sm + O_AI, LDO, m0, k0, lane, ih, il);
+        uint32_t ah[2][4], al[2][4], bh[3][2], bl[3][2];
+        load_a(sm + O_AR, LDO, m0, k0, lane, ah[0], al[0]);
+        load_a(sm + O_AI, LDO, m0, k0, lane, ah[1], al[1]);
 #pragma unroll
-        for (int nbk = 0; nbk < 3; ++nbk) {
-          load_b(sm + O_BY, LDO, nbk * 8, k0, lane, bh, bl);
-          mma3(acc[nbk], rh, rl, bh, bl);
-          mma3(acc[3 + nbk], ih, il, bh, bl);
-        }
+        for (int nbk = 0; nbk < 3; ++nbk) load_b(sm + O_BY, LDO, nbk * 8, k0, lane, bh[nbk], bl[nbk]);
+#pragma unroll
+        for (int term = 0; term < 3; ++term)
+#pragma unroll
+          for (int nbk = 0; nbk < 3; ++nbk)
+#pragma unroll
+            for (int ri = 0; ri < 2; ++ri)
+              mma(acc[3 * ri + nbk], term == 2 ? al[ri] : ah[ri], term == 1 ? bl[nbk] : bh[nbk]);
       }
     } else {
 #pragma unroll
       for (int k0 = 0; k0 < SBT; k0 += 8) {
-        uint32_t ah[4], al[4], b0h[2], b0l[2], b1h[2], b1l[2];
-        load_b(Bs0, LDV, 0, k0, lane, b0h, b0l);
-        load_b(Bs1, LDV, 0, k0, lane, b1h, b1l);
+        // tiles: 0-3 side [m-block][re | im], 4 corner
+        uint32_t ah[3][4], al[3][4], bh[3][2], bl[3][2];
+        load_a(Aside, LDO, 0, k0, lane, ah[0], al[0]);
+        load_a(Aside, LDO, 16, k0, lane, ah[1], al[1]);
+        load_aT(sm + O_K, LDT, 0, k0, lane, ah[2], al[2]);
+        load_bT(Bs0, LDT, 0, k0, lane, bh[0], bl[0]);
+        load_bT(Bs1, LDT, 0, k0, lane, bh[1], bl[1]);
+        load_bT(Bc, LDT, 0, k0, lane, bh[2], bl[2]);
 #pragma unroll
-        for (int mb = 0; mb < 2; ++mb) {
-          load_a(Aside, LDO, 16 * mb, k0, lane, ah, al);
-          mma3(acc[2 * mb], ah, al, b0h, b0l);
-          mma3(acc[2 * mb + 1], ah, al, b1h, b1l);
+        for (int term = 0; term < 3; ++term) {
+#pragma unroll
+          for (int tl = 0; tl < 4; ++tl)
+            mma(acc[tl], term == 2 ? al[tl >> 1] : ah[tl >> 1], term == 1 ? bl[tl & 1] : bh[tl & 1]);
+          mma(acc[4], term == 2 ? al[2] : ah[2], term == 1 ? bl[2] : bh[2]);
         }
-        load_a(sm + O_K, LDK, 0, k0, lane, ah, al);
-        load_b(Bc, LDV, 0, k0, lane, b0h, b0l);
-        mma3(acc[4], ah, al, b0h, b0l);
       }
     }
   }
