@@ -67,6 +67,7 @@ template <typename R> using C = typename Cx<R>::T;
 // ------------------------------------------------------------------ plan
 constexpr int TILE2 = 16;   // 2D spread tile edge (grid points); >= every KB half-width
 constexpr int TILE1 = 128;  // 1D spread tile length
+constexpr double WIN64_BYTES = 4.0 * (1 << 30);  // largest float64 window table of a plan
 constexpr int CHUNK2 = 512; // samples per 2D spread work item (load balance)
 constexpr int CHUNK1 = 512;
 
@@ -77,7 +78,7 @@ struct PrecData {
   double beta = 0;      // KB shape pi (2 - 1/sigma)
   // per-sample tables, sorted order
   R* frac = nullptr;    // [dims][M] fractional grid coordinate in [0, 1)
-  R* win = nullptr;     // float32 only: [M][dims][2m] window values phi(frac + m - 1 - a)
+  R* win = nullptr;     // [M][dims][2m] window values phi(frac + m - 1 - a); float64: may be absent
   C<R>* w = nullptr;    // [dims][M] interior factor (x factor carries sqrt(mu))
   C<R>* bf = nullptr;   // [dims][M][2b] boundary factors: left k=0..b-1 then right k=0..b-1
   R* deap = nullptr;    // [N] 1/psi(k_i) per coefficient index i (interior only)

@@ -31,32 +31,151 @@ namespace gs {
 namespace {
 using namespace dev;
 
-__device__ inline int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+// ---------------------------------------------------------------- shared-memory FFT
+// In-place DFT of nb rows of length n (a power of two) held contiguously in
+// shared memory: F[q] = sum_l f[l] e^{-+2 pi i l q / n} (+ for the inverse, no
+// scaling), natural order in and out.  Stockham's autosort form with radix-8
+// passes and, for the remaining factor, one radix-4 or radix-2 pass: the pass of
+// radix R after sub-transforms of length Ns (Ns = product of the earlier radices)
+// reads f[j + r n/R], r < R, multiplies by e^{-+2 pi i r (j mod Ns) / (Ns R)},
+// takes the R-point DFT in registers and writes it to (j div Ns) Ns R + (j mod Ns)
+// + r Ns.  Every thread holds PPT points per pass (the caller launches at least
+// nb n / PPT threads); a pass is load, barrier, compute and store, barrier.
+// Twiddles from the plan's table: tw[k tws] = e^{-2 pi i k / n}, k < n/2.
+template <typename R> __device__ inline C<R> csub(C<R> a, C<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+// a (-i), or a i for the inverse
+template <typename R> __device__ inline C<R> rot_q(C<R> a, bool inv) { return inv ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
 
-// In-place radix-2 DIT FFT of nb sequences of length n held in shared memory in
-// bit-reversed order; output in natural order.  tw[k] = exp(-2 pi i k/n).
-template <typename R>
-__device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restrict__ tw, bool inverse,
-                         int tws = 1) {
-  const int half_total = nb * (n >> 1);
-  for (int s = 1; s <= logn; ++s) {
-    const int half = 1 << (s - 1);
-    const int step = n >> s;
-    for (int t = threadIdx.x; t < half_total; t += blockDim.x) {
-      int seq = t / (n >> 1);
-      int bt = t - seq * (n >> 1);
-      int grp = bt >> (s - 1);
-      int pos = bt & (half - 1);
-      int i0 = seq * n + grp * 2 * half + pos;
-      int i1 = i0 + half;
-      C<R> w = tw[pos * step * tws];
-      if (inverse) w.y = -w.y;
-      C<R> a = buf[i0];
-      C<R> bb = cmul(buf[i1], w);
-      buf[i0] = cadd(a, bb);
-      buf[i1] = mk<R>(a.x - bb.x, a.y - bb.y);
+template <typename R> __device__ inline void dft_reg2(C<R>* v, bool) {
+  const C<R> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub<R>(a, b);
+}
+template <typename R> __device__ inline void dft4(C<R>& v0, C<R>& v1, C<R>& v2, C<R>& v3, bool inv) {
+  const C<R> a0 = cadd(v0, v2), a1 = csub<R>(v0, v2), a2 = cadd(v1, v3), w = rot_q<R>(csub<R>(v1, v3), inv);
+  v0 = cadd(a0, a2);
+  v2 = csub<R>(a0, a2);
+  v1 = cadd(a1, w);
+  v3 = csub<R>(a1, w);
+}
+template <typename R> __device__ inline void dft_reg4(C<R>* v, bool inv) { dft4<R>(v[0], v[1], v[2], v[3], inv); }
+// 8 points: two 4-point DFTs of the even and odd samples, combined with e^{-+i pi q/4}
+template <typename R> __device__ inline void dft_reg8(C<R>* v, bool inv) {
+  C<R> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<R>(e0, e1, e2, e3, inv);
+  dft4<R>(o0, o1, o2, o3, inv);
+  const R h = (R)0.70710678118654752440;  // 1/sqrt(2)
+  const C<R> t1 = inv ? mk<R>((o1.x - o1.y) * h, (o1.x + o1.y) * h) : mk<R>((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+  const C<R> t2 = rot_q<R>(o2, inv);
+  const C<R> t3 = inv ? mk<R>((-o3.x - o3.y) * h, (o3.x - o3.y) * h) : mk<R>((o3.y - o3.x) * h, (-o3.x - o3.y) * h);
+  v[0] = cadd(e0, o0);
+  v[4] = csub<R>(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub<R>(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub<R>(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub<R>(e3, t3);
+}
+template <typename R, int RAD> __device__ inline void dft_reg(C<R>* v, bool inv) {
+  if constexpr (RAD == 8) dft_reg8<R>(v, inv);
+  else if constexpr (RAD == 4) dft_reg4<R>(v, inv);
+  else dft_reg2<R>(v, inv);
+}
+
+// one pass: radix RAD = 2^lr, n / RAD = 2^lgq butterflies per row, Ns = 2^lgNs
+template <typename R, int RAD, int PPT>
+__device__ inline void fft_pass(C<R>* buf, int nb, int n, int lgq, int lgNs, const C<R>* __restrict__ tw, int tws,
+                                bool inv) {
+  constexpr int NB = PPT / RAD;  // butterflies per thread
+  constexpr int lr = (RAD == 8) ? 3 : (RAD == 4) ? 2 : 1;
+  const int q = 1 << lgq, Ns = 1 << lgNs;
+  const int nbf = nb << lgq;
+  C<R> v[NB][RAD];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int bi = threadIdx.x + k * blockDim.x;
+    if (bi < nbf) {
+      const C<R>* src = buf + (bi >> lgq) * n + (bi & (q - 1));
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) v[k][r] = src[r * q];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int half = (n * tws) >> 1;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int bi = threadIdx.x + k * blockDim.x;
+    if (bi < nbf) {
+      const int row = bi >> lgq, j = bi & (q - 1), jm = j & (Ns - 1);
+      if (lgNs > 0) {
+        // e^{-+2 pi i r jm / (Ns RAD)} = table entry r jm (n / (Ns RAD)) tws, below n tws
+        const int step = (jm << (lgq - lgNs)) * tws;
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          const int e = r * step;
+          C<R> w = (e < half) ? tw[e] : tw[e - half];
+          if (e >= half) w = mk<R>(-w.x, -w.y);
+          if (inv) w.y = -w.y;
+          v[k][r] = cmul(v[k][r], w);
+        }
+      }
+      dft_reg<R, RAD>(v[k], inv);
+      C<R>* dst = buf + row * n + ((j >> lgNs) << (lgNs + lr)) + jm;
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) dst[r * Ns] = v[k][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int PPT>
+__device__ void fft_smem(C<R>* buf, int nb, int n, int logn, const C<R>* __restrict__ tw, bool inverse, int tws = 1) {
+  int lgNs = 0;
+  while (lgNs < logn) {
+    const int left = logn - lgNs;
+    if (left >= 3) {
+      fft_pass<R, 8, PPT>(buf, nb, n, logn - 3, lgNs, tw, tws, inverse);
+      lgNs += 3;
+    } else if (left == 2) {
+      fft_pass<R, 4, PPT>(buf, nb, n, logn - 2, lgNs, tw, tws, inverse);
+      lgNs += 2;
+    } else {
+      fft_pass<R, 2, PPT>(buf, nb, n, logn - 1, lgNs, tw, tws, inverse);
+      lgNs += 1;
+    }
+  }
+}
+constexpr int PPT_ROW = 8;  // points per thread and pass
+// threads of an FFT CTA: PPT_ROW points each for its nb rows of length n (at most
+// 1024 threads: n <= 8192 per CTA, which covers the single-CTA 1D transforms,
+// n < FOUR_STEP_N, the four-step rows and the 2D passes, n <= 1024)
+inline int fft_threads(int nb, int n) {
+  const int t = ((nb * n / PPT_ROW + 31) / 32) * 32;
+  return t < 64 ? 64 : (t > 1024 ? 1024 : t);
+}
+
+// for t = threadIdx.x, + blockDim.x, ... < total: v = load(t), then store(t, v), in
+// groups of LB per thread whose loads are all issued before the group's stores
+// (the pass kernels have few warps, so memory latency is hidden by batching)
+template <typename R> struct Cv {  // a value and whether to store it
+  C<R> v;
+  bool ok;
+};
+template <int LB, typename T, typename L, typename S>
+__device__ inline void batched(int total, L load, S store) {
+  for (int base = threadIdx.x; base < total; base += LB * blockDim.x) {
+    T v[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = base + u * blockDim.x;
+      if (t < total) v[u] = load(t);
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int t = base + u * blockDim.x;
+      if (t < total) store(t, v[u]);
+    }
   }
 }
 
@@ -73,11 +192,11 @@ __global__ void k_fwd1d_fft(const C<R>* __restrict__ x, const R* __restrict__ de
     R dv = deap[i];
     if (dv != (R)0) {
       int idx = (int)((i - N / 2) & (n - 1));
-      buf[brev(idx, logn)] = cscale(x[i], dv);
+      buf[idx] = cscale(x[i], dv);
     }
   }
   __syncthreads();
-  fft_smem<R>(buf, 1, n, logn, tw, false);
+  fft_smem<R, PPT_ROW>(buf, 1, n, logn, tw, false);
   for (int i = threadIdx.x; i < n; i += blockDim.x) grid[i] = buf[i];
 }
 
@@ -113,10 +232,10 @@ __global__ void k_fwd1d_cols(const C<R>* __restrict__ x, const R* __restrict__ d
       const R dv = deap[i];
       if (dv != (R)0) v = cscale(x[i], dv);
     }
-    buf[brev(j2, logn2)] = v;
+    buf[j2] = v;
   }
   __syncthreads();
-  fft_smem<R>(buf, 1, n2, logn2, tw, false, n / n2);
+  fft_smem<R, PPT_ROW>(buf, 1, n2, logn2, tw, false, n / n2);
   for (int k2 = threadIdx.x; k2 < n2; k2 += blockDim.x)
     B[(int64_t)j1 * n2 + k2] = cmul(buf[k2], tw_full<R>(tw, (int64_t)j1 * k2, n, false));
 }
@@ -128,9 +247,9 @@ __global__ void k_fwd1d_rows(const C<R>* __restrict__ B, int n, int n1, int logn
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int k2 = blockIdx.x;
-  for (int j1 = threadIdx.x; j1 < n1; j1 += blockDim.x) buf[brev(j1, logn1)] = B[(int64_t)j1 * n2 + k2];
+  for (int j1 = threadIdx.x; j1 < n1; j1 += blockDim.x) buf[j1] = B[(int64_t)j1 * n2 + k2];
   __syncthreads();
-  fft_smem<R>(buf, 1, n1, logn1, tw, false, n / n1);
+  fft_smem<R, PPT_ROW>(buf, 1, n1, logn1, tw, false, n / n1);
   for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) grid[k2 + (int64_t)n2 * k1] = buf[k1];
 }
 
@@ -141,9 +260,9 @@ __global__ void k_adj1d_rows(const C<R>* __restrict__ grid, int n, int n1, int l
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int k2 = blockIdx.x;
-  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) buf[brev(k1, logn1)] = grid[k2 + (int64_t)n2 * k1];
+  for (int k1 = threadIdx.x; k1 < n1; k1 += blockDim.x) buf[k1] = grid[k2 + (int64_t)n2 * k1];
   __syncthreads();
-  fft_smem<R>(buf, 1, n1, logn1, tw, true, n / n1);
+  fft_smem<R, PPT_ROW>(buf, 1, n1, logn1, tw, true, n / n1);
   for (int j1 = threadIdx.x; j1 < n1; j1 += blockDim.x)
     Cb[(int64_t)k2 * n1 + j1] = cmul(buf[j1], tw_full<R>(tw, (int64_t)j1 * k2, n, true));
 }
@@ -157,9 +276,9 @@ __global__ void k_adj1d_cols(const C<R>* __restrict__ Cb, const R* __restrict__ 
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int j1 = blockIdx.x;
-  for (int k2 = threadIdx.x; k2 < n2; k2 += blockDim.x) buf[brev(k2, logn2)] = Cb[(int64_t)k2 * n1 + j1];
+  for (int k2 = threadIdx.x; k2 < n2; k2 += blockDim.x) buf[k2] = Cb[(int64_t)k2 * n1 + j1];
   __syncthreads();
-  fft_smem<R>(buf, 1, n2, logn2, tw, true, n / n2);
+  fft_smem<R, PPT_ROW>(buf, 1, n2, logn2, tw, true, n / n2);
   for (int j2 = threadIdx.x; j2 < n2; j2 += blockDim.x) {
     const int l = j1 + n1 * j2;
     const int64_t k = (l < n / 2) ? l : (int64_t)l - n;
@@ -290,9 +409,9 @@ __global__ void k_adj1d_fft(const C<R>* __restrict__ grid, const R* __restrict__
                             C<R>* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) buf[brev(i, logn)] = grid[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) buf[i] = grid[i];
   __syncthreads();
-  fft_smem<R>(buf, 1, n, logn, tw, true);
+  fft_smem<R, PPT_ROW>(buf, 1, n, logn, tw, true);
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     C<R> v;
     if (i < b) v = bsum[i];
@@ -311,18 +430,23 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
-  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) buf[i] = mk<R>(0, 0);
+  // grid point l of row r holds coefficient i = l + N/2 (mod n), deapodised, or 0
+  batched<PPT_ROW, C<R>>(
+      nr * n,
+      [&](int t) {
+        const int r = t >> logn, l = t & (n - 1);
+        const int i = (l + N / 2) & (n - 1);
+        C<R> v = mk<R>(0, 0);
+        if (i < N) {
+          const R dv = deap[i];
+          const C<R> xv = x[(int64_t)(j0 + r) * N + i];
+          if (dv != (R)0) v = cscale(xv, dv);
+        }
+        return v;
+      },
+      [&](int t, C<R> v) { buf[t] = v; });
   __syncthreads();
-  for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-    int r = t / N, i = t - r * N;
-    R dv = deap[i];
-    if (dv != (R)0) {
-      int idx = (i - N / 2) & (n - 1);
-      buf[r * n + brev(idx, logn)] = cscale(x[(int64_t)(j0 + r) * N + i], dv);
-    }
-  }
-  __syncthreads();
-  fft_smem<R>(buf, nr, n, logn, tw, false);
+  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, false);
   for (int t = threadIdx.x; t < nr * n; t += blockDim.x) hbuf[(int64_t)j0 * n + t] = buf[t];
 }
 
@@ -337,26 +461,30 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
   const int c0 = blockIdx.x * cols;
   const int ntot = n + 2 * b;
   const int nc = min(cols, ntot - c0);
-  for (int i = threadIdx.x; i < nc * n; i += blockDim.x) buf[i] = mk<R>(0, 0);
+  // position l of column c holds row j = l + N/2 (mod n) of the column, deapodised, or 0
+  batched<PPT_ROW, C<R>>(
+      nc * n,
+      [&](int t) {
+        const int c = t >> logn, l = t & (n - 1);
+        const int j = (l + N / 2) & (n - 1);
+        C<R> v = mk<R>(0, 0);
+        if (j < N) {
+          const R dv = deap[j];
+          const int col = c0 + c;
+          C<R> u;
+          if (col < n) {
+            u = hbuf[(int64_t)j * n + col];
+          } else {
+            const int k = col - n;
+            u = x[(int64_t)j * N + ((k < b) ? k : (N - 1 - (k - b)))];
+          }
+          if (dv != (R)0) v = cscale(u, dv);
+        }
+        return v;
+      },
+      [&](int t, C<R> v) { buf[t] = v; });
   __syncthreads();
-  for (int t = threadIdx.x; t < nc * N; t += blockDim.x) {
-    int j = t / nc, c = t - j * nc;
-    R dv = deap[j];
-    if (dv == (R)0) continue;
-    int col = c0 + c;
-    C<R> v;
-    if (col < n) {
-      v = hbuf[(int64_t)j * n + col];
-    } else {
-      int k = col - n;
-      int i = (k < b) ? k : (N - 1 - (k - b));
-      v = x[(int64_t)j * N + i];
-    }
-    int idx = (j - N / 2) & (n - 1);
-    buf[c * n + brev(idx, logn)] = cscale(v, dv);
-  }
-  __syncthreads();
-  fft_smem<R>(buf, nc, n, logn, tw, false);
+  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tw, false);
   for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
     int c = t / n, l = t - c * n;
     int col = c0 + c;
@@ -388,14 +516,29 @@ __global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<
   const int gy = blockIdx.y * tile + threadIdx.x;
   if (gx >= n || gy >= n) return;
   const int PW = tile + 2 * m;
+  // neighbour bins along each axis in the order -1, 0, +1, each bin once (as neighbours())
+  const int bx = gx / tile, by = gy / tile;
   int cx[3], cy[3];
-  int ncx = neighbours(gx / tile, nbx, cx), ncy = neighbours(gy / tile, nbx, cy);
+  bool vx[3], vy[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    cx[d] = (bx + d - 1) & (nbx - 1);
+    cy[d] = (by + d - 1) & (nbx - 1);
+  }
+  vx[0] = vy[0] = true;
+  vx[1] = cx[1] != cx[0];
+  vy[1] = cy[1] != cy[0];
+  vx[2] = cx[2] != cx[0] && cx[2] != cx[1];
+  vy[2] = cy[2] != cy[0] && cy[2] != cy[1];
   C<R> acc = mk<R>(0, 0);
-  for (int iy = 0; iy < ncy; ++iy)
-    for (int ix = 0; ix < ncx; ++ix) {
-      int nb = cy[iy] * nbx + cx[ix];
-      int qx0 = (gx - cx[ix] * tile + m) & (n - 1);
-      int qy0 = (gy - cy[iy] * tile + m) & (n - 1);
+#pragma unroll
+  for (int iy = 0; iy < 3; ++iy)
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      if (!vx[ix] || !vy[iy]) continue;
+      const int nb = cy[iy] * nbx + cx[ix];
+      const int qx0 = (gx - cx[ix] * tile + m) & (n - 1);
+      const int qy0 = (gy - cy[iy] * tile + m) & (n - 1);
       if (qx0 >= PW || qy0 >= PW) continue;  // this bin's tiles do not reach (gx, gy)
       for (int wi = work_start[nb]; wi < work_start[nb + 1]; ++wi)
         for (int qx = qx0; qx < PW; qx += n)
@@ -451,28 +594,33 @@ __global__ void k_adj2d_pass2(const C<R>* __restrict__ grid, const C<R>* __restr
   const int c0 = blockIdx.x * cols;
   const int ntot = n + 2 * b;
   const int nc = min(cols, ntot - c0);
-  for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
-    int c = t / n, l = t - c * n;
-    int col = c0 + c;
-    C<R> v = (col < n) ? grid[(int64_t)col * n + l] : side[(int64_t)(col - n) * n + l];
-    buf[c * n + brev(l, logn)] = v;
-  }
+  batched<PPT_ROW, C<R>>(
+      nc * n,
+      [&](int t) {
+        const int c = t >> logn, l = t & (n - 1), col = c0 + c;
+        return (col < n) ? grid[(int64_t)col * n + l] : side[(int64_t)(col - n) * n + l];
+      },
+      [&](int t, C<R> v) { buf[t] = v; });
   __syncthreads();
-  fft_smem<R>(buf, nc, n, logn, tw, true);
-  for (int t = threadIdx.x; t < nc * N; t += blockDim.x) {
-    int j = t / nc, c = t - j * nc;
-    R dv = deap[j];
-    if (dv == (R)0) continue;
-    int col = c0 + c;
-    C<R> v = cscale(buf[c * n + ((j - N / 2) & (n - 1))], dv);
-    if (col < n) {
-      hbuf[(int64_t)j * n + col] = v;
-    } else {
-      int k = col - n;
-      int i = (k < b) ? k : (N - 1 - (k - b));
-      z[(int64_t)j * N + i] = v;
-    }
-  }
+  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tw, true);
+  // t = c + nc j: column c of row j, so that consecutive threads write neighbouring columns
+  batched<PPT_ROW, Cv<R>>(
+      nc * N,
+      [&](int t) {
+        const int j = t / nc, c = t - j * nc;
+        const R dv = deap[j];
+        return Cv<R>{cscale(buf[c * n + ((j - N / 2) & (n - 1))], dv), dv != (R)0};
+      },
+      [&](int t, Cv<R> o) {
+        if (!o.ok) return;
+        const int j = t / nc, col = c0 + t - j * nc;
+        if (col < n) {
+          hbuf[(int64_t)j * n + col] = o.v;
+        } else {
+          const int k = col - n;
+          z[(int64_t)j * N + ((k < b) ? k : (N - 1 - (k - b)))] = o.v;
+        }
+      });
 }
 
 // adjoint pass 1: inverse x-transform of hbuf rows (interior j) or of the y-side
@@ -487,36 +635,31 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
   const int b2 = 2 * b;
-  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
-    int r = t / n, l = t - r * n;
-    int j = j0 + r;
-    C<R> v;
-    if (j >= b && j < N - b) {
-      v = hbuf[(int64_t)j * n + l];
-    } else {
-      int k = (j < b) ? j : b + (N - 1 - j);
-      v = side1[(int64_t)k * n + l];
-    }
-    buf[r * n + brev(l, logn)] = v;
-  }
+  batched<PPT_ROW, C<R>>(
+      nr * n,
+      [&](int t) {
+        const int r = t >> logn, l = t & (n - 1), j = j0 + r;
+        if (j >= b && j < N - b) return hbuf[(int64_t)j * n + l];
+        const int k = (j < b) ? j : b + (N - 1 - j);
+        return side1[(int64_t)k * n + l];
+      },
+      [&](int t, C<R> v) { buf[t] = v; });
   __syncthreads();
-  fft_smem<R>(buf, nr, n, logn, tw, true);
-  for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-    int r = t / N, i = t - r * N;
-    int j = j0 + r;
-    R dv = deap[i];
-    C<R> v;
-    if (dv != (R)0) {
-      v = cscale(buf[r * n + ((i - N / 2) & (n - 1))], dv);
-    } else {
-      bool jb = (j < b) || (j >= N - b);
-      if (!jb) continue;  // x-side entries come from pass 2
-      int kx = (i < b) ? i : b + (N - 1 - i);
-      int ky = (j < b) ? j : b + (N - 1 - j);
-      v = corner[ky * b2 + kx];
-    }
-    z[(int64_t)j * N + i] = v;
-  }
+  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, true);
+  batched<PPT_ROW, Cv<R>>(
+      nr * N,
+      [&](int t) {
+        const int r = t / N, i = t - r * N, j = j0 + r;
+        const R dv = deap[i];
+        if (dv != (R)0) return Cv<R>{cscale(buf[r * n + ((i - N / 2) & (n - 1))], dv), true};
+        if (j >= b && j < N - b) return Cv<R>{mk<R>(0, 0), false};  // x-side entries come from pass 2
+        const int kx = (i < b) ? i : b + (N - 1 - i);
+        const int ky = (j < b) ? j : b + (N - 1 - j);
+        return Cv<R>{corner[ky * b2 + kx], true};
+      },
+      [&](int t, Cv<R> o) {
+        if (o.ok) z[(int64_t)(j0 + t / N) * N + t % N] = o.v;
+      });
 }
 
 template <typename R>
@@ -562,7 +705,7 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
       gs_status s = set_smem<R>((const void*)k_fwd1d_fft<R>, sh);
       if (s != GS_OK) return s;
       GS_LAUNCH(pname<R>("fwd1d_fft<f32>", "fwd1d_fft<f64>"), st,
-                k_fwd1d_fft<R><<<1, 1024, sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
+                k_fwd1d_fft<R><<<1, fft_threads(1, n), sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
     }
     GS_LAUNCH(pname<R>("interp1d<f32>", "interp1d<f64>"), st,
               k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
@@ -573,14 +716,14 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
-              k_fwd2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw,
+              k_fwd2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw,
                                                                         D.hbuf));
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
-              k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, 256, sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
+              k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
                                                                                 cols, D.tw, D.grid, D.side));
     gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part);
     if (si != GS_OK) return si;
@@ -623,7 +766,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
       gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
       if (s != GS_OK) return s;
       GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
-                k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+                k_adj1d_fft<R><<<1, fft_threads(1, n), shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
     }
   } else {
     const int PW = tile + 2 * m;
@@ -648,14 +791,14 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
-              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
+              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
                                                                               cols, D.tw, D.hbuf, z));
     const int rows = 1;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
-              k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z));
   }
@@ -700,7 +843,7 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
       gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
       if (s != GS_OK) return s;
       GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
-                k_adj1d_fft<R><<<1, 1024, shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
+                k_adj1d_fft<R><<<1, fft_threads(1, n), shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
     }
   } else {
     const int PW = tile + 2 * m;
@@ -725,14 +868,14 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
-              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, 256, sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
+              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
                                                                               cols, D.tw, D.hbuf, z));
     const int rows = 1;
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
-              k_adj2d_pass1<R><<<(N + rows - 1) / rows, 256, sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z));
   }

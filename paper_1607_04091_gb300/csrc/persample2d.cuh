@@ -16,8 +16,8 @@ namespace dev {
 
 constexpr int NCQ = (GS_MAX_B * GS_MAX_B + 31) / 32;  // corner channels per lane
 
-// window values of the W taps of sample s along dimension d: float32 from the
-// plan's table, float64 evaluated exactly
+// window values of the W taps of sample s along dimension d: from the plan's
+// table (float32 always, float64 when the plan holds one), else evaluated
 template <typename R, int W> struct WinEval;
 template <int W> struct WinEval<float, W> {
   static __device__ inline void get(const float* __restrict__ win, int64_t s, int d, float, float, float* out) {
@@ -27,9 +27,15 @@ template <int W> struct WinEval<float, W> {
   }
 };
 template <int W> struct WinEval<double, W> {
-  static __device__ inline void get(const double*, int64_t, int, double t, double beta, double* out) {
+  static __device__ inline void get(const double* win, int64_t s, int d, double t, double beta, double* out) {
+    if (win) {  // the plan's table
+      const double* p = win + ((int64_t)s * 2 + d) * W;
 #pragma unroll
-    for (int a = 0; a < W; ++a) out[a] = kb_window(t + (double)(W / 2 - 1 - a), W / 2, beta);
+      for (int a = 0; a < W; ++a) out[a] = __ldg(p + a);
+    } else {
+#pragma unroll
+      for (int a = 0; a < W; ++a) out[a] = kb_window(t + (double)(W / 2 - 1 - a), W / 2, beta);
+    }
   }
 };
 

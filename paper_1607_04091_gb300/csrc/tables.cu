@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "gs_internal.h"
+#include "device_common.cuh"
 
 namespace gs {
 
@@ -323,6 +324,19 @@ gs_status dalloc(T** p, size_t count) {
     if (s_ != GS_OK) return s_;    \
   } while (0)
 
+// float64 window values phi(frac + m - 1 - a) of the 2m taps of every sample and
+// dimension, [s][d][a], by the same function the kernels use without a table
+__global__ void k_win64(const double* __restrict__ frac, int64_t M, int dims, int m, double beta,
+                        double* __restrict__ win) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= M * dims) return;
+  const int d = (int)(g / M);
+  const int64_t s = g - (int64_t)d * M;
+  const double t = frac[g];
+  double* out = win + (s * dims + d) * (2 * m);
+  for (int a = 0; a < 2 * m; ++a) out[a] = dev::kb_window(t + (double)(m - 1 - a), m, beta);
+}
+
 template <typename R>
 gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
   D.m = m;
@@ -330,7 +344,10 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
   const int64_t M = P->M, n = P->n, N = P->N;
   const int dims = P->dims, b = P->b, b2 = 2 * b;
   GS_TRY(dalloc(&D.frac, (size_t)dims * M));
-  if (sizeof(R) == 4) GS_TRY(dalloc(&D.win, (size_t)dims * M * 2 * m));
+  // window values of every tap: float32 always; float64 while the table stays
+  // within WIN64_BYTES (else the kernels evaluate the window per tap)
+  if (sizeof(R) == 4 || (double)dims * M * 2 * m * sizeof(double) <= (double)WIN64_BYTES)
+    GS_TRY(dalloc(&D.win, (size_t)dims * M * 2 * m));
   GS_TRY(dalloc(&D.w, (size_t)dims * M));
   GS_TRY(dalloc(&D.bf, (size_t)dims * M * (b2 > 0 ? b2 : 1)));
   GS_TRY(dalloc(&D.deap, (size_t)N));
@@ -505,6 +522,8 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
   k_tables<<<(tot + 127) / 128, 128, 0, st>>>(P->xi_sorted, ms, M, dims, P->J, P->p, P->b, K.mu1, K.mu2,
                                              P->n, P->d.w, P->d.bf, P->d.frac, P->f.w, P->f.bf, P->f.frac,
                                              P->f.m, P->f.beta, P->f.win);
+  if (P->d.win)
+    k_win64<<<(tot + 127) / 128, 128, 0, st>>>(P->d.frac, M, dims, P->d.m, P->d.beta, P->d.win);
   k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->d.m, P->d.beta, P->d.deap, nullptr, 0);
   k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->f.m, P->f.beta, nullptr, P->f.deap, 1);
   k_twiddle<<<(P->n / 2 + 255) / 256, 256, 0, st>>>(P->n, P->d.tw, P->f.tw);
