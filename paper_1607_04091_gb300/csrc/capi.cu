@@ -103,6 +103,11 @@ static void free_plan(Plan* P) {
   for (int i = 0; i < 2; ++i)
     if (P->solve_exec[i]) cudaGraphExecDestroy(P->solve_exec[i]);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  for (int i = 0; i < 3; ++i) {
+    if (P->aux[i]) cudaStreamDestroy(P->aux[i]);
+    if (P->ev_fork[i]) cudaEventDestroy(P->ev_fork[i]);
+    if (P->ev_join[i]) cudaEventDestroy(P->ev_join[i]);
+  }
   free_prec_d(P->d);
   free_prec_f(P->f);
 }
@@ -191,6 +196,11 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
   }
   GS_CUDA(cudaGetDevice(&P->dev));
   GS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 3; ++i) {
+    GS_CUDA(cudaStreamCreateWithFlags(&P->aux[i], cudaStreamNonBlocking));
+    GS_CUDA(cudaEventCreateWithFlags(&P->ev_fork[i], cudaEventDisableTiming));
+    GS_CUDA(cudaEventCreateWithFlags(&P->ev_join[i], cudaEventDisableTiming));
+  }
   gs_status s = build_plan(P, xi, weights, (cudaStream_t)stream);
   if (s != GS_OK) {
     free_plan(P);

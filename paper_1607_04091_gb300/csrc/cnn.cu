@@ -286,12 +286,6 @@ gs_status dalloc(T** p, size_t count) {
   return GS_OK;
 }
 
-#define GS_TRY(x)               \
-  do {                          \
-    gs_status s_ = (x);         \
-    if (s_ != GS_OK) return s_; \
-  } while (0)
-
 // forward through all layers with float32 weights, keeping activations
 gs_status forward_train(gs_cnn_s* N, const float* u, int B, cudaStream_t st) {
   const int64_t img = (int64_t)2 * N->H * N->W * B;

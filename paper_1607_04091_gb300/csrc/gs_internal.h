@@ -40,6 +40,12 @@ gs_status cuda_fail(cudaError_t e, const char* what);
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return gs::cuda_fail(e_, #call); \
   } while (0)
+// return a failed status to the caller
+#define GS_TRY(x)               \
+  do {                          \
+    gs_status s_ = (x);         \
+    if (s_ != GS_OK) return s_; \
+  } while (0)
 
 // ------------------------------------------------------------------ tracing
 // When enabled (gs_profile), every wrapped launch records a CUDA event pair on
@@ -132,9 +138,33 @@ struct Plan {
   double* r64 = nullptr;    // M, FP64 residual (complex128)
   double* x64 = nullptr;    // ncoef complex128 accumulator
   cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  // side branches of an apply or CG step: 0, 1 the partial reductions of the 2D
+  // adjoint, 2 the step length of CG (see fork_aux / join_aux)
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork[3] = {nullptr, nullptr, nullptr}, ev_join[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};  // whole mixed solve as one graph [zero, given start]
   bool solve_graph_failed = false;
 };
+
+// Work launched on side_stream(P, st, i) between fork_aux(P, st, i) and
+// join_aux(P, st, i) runs after everything enqueued on st before the fork and
+// before everything enqueued on st after the join, concurrently with st in
+// between; inside a stream capture the two become parallel branches of the
+// graph.  With tracing on, the branch is st itself, so that each launch's event
+// pair times that kernel alone.
+inline cudaStream_t side_stream(Plan* P, cudaStream_t st, int i) { return prof_on() ? st : P->aux[i]; }
+inline gs_status fork_aux(Plan* P, cudaStream_t st, int i) {
+  if (prof_on()) return GS_OK;
+  GS_CUDA(cudaEventRecord(P->ev_fork[i], st));
+  GS_CUDA(cudaStreamWaitEvent(P->aux[i], P->ev_fork[i], 0));
+  return GS_OK;
+}
+inline gs_status join_aux(Plan* P, cudaStream_t st, int i) {
+  if (prof_on()) return GS_OK;
+  GS_CUDA(cudaEventRecord(P->ev_join[i], P->aux[i]));
+  GS_CUDA(cudaStreamWaitEvent(st, P->ev_join[i], 0));
+  return GS_OK;
+}
 
 // implemented in tables.cu
 gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStream_t st);

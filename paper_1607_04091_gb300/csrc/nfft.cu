@@ -547,6 +547,42 @@ __global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<
   grid[(int64_t)gx * n + gy] = acc;
 }
 
+// The same sum for 16 x 16 tiles and at least 3 bins per axis (no bin is its own
+// neighbour): CTA per tile, thread per point; the item ranges of the 3 x 3
+// neighbour bins are read once per CTA.  Bins and items are visited in the order
+// of k_reduce2d_grid, so the sums are identical.
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restrict__ work_start,
+                                                         const C<R>* __restrict__ part, int64_t stride, int nbx,
+                                                         int m, int n, C<R>* __restrict__ grid) {
+  constexpr int T = 16;
+  __shared__ int rng[9][2];  // [iy * 3 + ix] -> first, end item
+  const int bx = blockIdx.x, by = blockIdx.y;
+  if (threadIdx.x < 9) {
+    const int iy = threadIdx.x / 3, ix = threadIdx.x - 3 * iy;
+    const int nb = ((by + iy - 1) & (nbx - 1)) * nbx + ((bx + ix - 1) & (nbx - 1));
+    rng[threadIdx.x][0] = work_start[nb];
+    rng[threadIdx.x][1] = work_start[nb + 1];
+  }
+  __syncthreads();
+  const int lx = threadIdx.x >> 4, ly = threadIdx.x & 15;
+  const int PW = T + 2 * m;
+  C<R> acc = mk<R>(0, 0);
+#pragma unroll
+  for (int iy = 0; iy < 3; ++iy) {
+    const int qy = ly - T * (iy - 1) + m;
+    if (qy < 0 || qy >= PW) continue;
+#pragma unroll
+    for (int ix = 0; ix < 3; ++ix) {
+      const int qx = lx - T * (ix - 1) + m;
+      if (qx < 0 || qx >= PW) continue;
+      const int r0 = rng[iy * 3 + ix][0], r1 = rng[iy * 3 + ix][1];
+      for (int wi = r0; wi < r1; ++wi) acc = cadd(acc, part[wi * stride + qx * PW + qy]);
+    }
+  }
+  grid[(int64_t)(bx * T + lx) * n + by * T + ly] = acc;
+}
+
 // side grids: which = 0 -> x-side k along y (segments S0; the work items of
 // the neighbouring bin rows are contiguous), which = 1 -> y-side k along x
 // (segments S1; work items of the neighbouring bin columns from the column
@@ -773,18 +809,33 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     const int wsz = PW * PW + 2 * b2 * PW;
     gs_status s = launch_spread2d<R>(P, D, y, perm, D.part, st);
     if (s != GS_OK) return s;
-    dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
-              k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
-                                                    D.grid));
+    // the three reductions of the partials read the same input: side segments and
+    // corners on two side branches, the grid on st
     if (b2 > 0) {
+      GS_TRY(fork_aux(P, st, 0));
+      GS_TRY(fork_aux(P, st, 1));
+      cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
       dim3 sg(P->nbx, b2, 2);
-      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
-                k_reduce2d_side<R><<<sg, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, D.part,
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a0,
+                k_reduce2d_side<R><<<sg, 256, 0, a0>>>(P->work_start, P->wcol, P->wcol_start, D.part,
                                                         D.part_stride, P->nbx, tile, m, n, b2, D.side));
-      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
-                k_reduce_chan<R><<<b2 * b2, 256, 0, st>>>(D.part, D.part_stride, wsz, b2 * b2, P->nwork,
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), a1,
+                k_reduce_chan<R><<<b2 * b2, 256, 0, a1>>>(D.part, D.part_stride, wsz, b2 * b2, P->nwork,
                                                            D.corner));
+    }
+    dim3 rg(P->nbx, P->nby), rb(tile, tile);
+    if (tile == 16 && P->nbx >= 3)
+      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+                k_reduce2d_grid16<R><<<rg, 256, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, m, n,
+                                                         D.grid));
+    else
+      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+                k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
+                                                      D.grid));
+    if (b2 > 0) {
+      GS_CUDA(cudaGetLastError());
+      GS_TRY(join_aux(P, st, 0));
+      GS_TRY(join_aux(P, st, 1));
     }
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);

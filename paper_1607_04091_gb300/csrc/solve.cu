@@ -243,16 +243,22 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
     if (s != GS_OK) return s;
     GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<RED_BLOCKS, 256, 0, st>>>(D.vq, M, P->red, P->flag));
   }
-  GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, np, P->scal, P->flag));
   // ||s||^2 partials go after the ||q||^2 ones
   double* red_s = P->red + std::max<int64_t>(P->nwork, RED_BLOCKS);
   const int gs = grid_for(nc);
   if (normal_eq) {
+    // alpha on a side branch: only the update after T^H q needs it
+    GS_TRY(fork_aux(P, st, 2));
+    cudaStream_t a2 = side_stream(P, st, 2);
+    GS_LAUNCH("cgls_scalar", a2, k_alpha<<<1, 256, 0, a2>>>(P->red, np, P->scal, P->flag));
+    GS_CUDA(cudaGetLastError());
     s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
     if (s != GS_OK) return s;
+    GS_TRY(join_aux(P, st, 2));
     GS_LAUNCH("cgls_axpy", st,
               k_update_xs<R><<<gs, 256, 0, st>>>(D.vx, D.vp, D.vs, D.vz, nc, P->scal, P->flag, red_s));
   } else {
+    GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, np, P->scal, P->flag));
     GS_LAUNCH("cgls_axpy", st,
               k_update_xr<R><<<grid_for(nc + M), 256, 0, st>>>(D.vx, D.vp, nc, D.vr, D.vq, M, P->scal, P->flag));
     s = apply_TH<R>(P, D, D.vr, D.vs, nullptr, st);
@@ -389,12 +395,6 @@ __global__ void k_addto(double2* __restrict__ x, const C<R>* __restrict__ d, int
     x[i] = v;
   }
 }
-
-#define GS_TRY(x)               \
-  do {                          \
-    gs_status s_ = (x);         \
-    if (s_ != GS_OK) return s_; \
-  } while (0)
 
 // r64 = y64 - T x64 (float64 forward apply)
 gs_status residual64(Plan* P, cudaStream_t st) {

@@ -318,12 +318,6 @@ gs_status dalloc(T** p, size_t count) {
   return GS_OK;
 }
 
-#define GS_TRY(x)                  \
-  do {                             \
-    gs_status s_ = (x);            \
-    if (s_ != GS_OK) return s_;    \
-  } while (0)
-
 // float64 window values phi(frac + m - 1 - a) of the 2m taps of every sample and
 // dimension, [s][d][a], by the same function the kernels use without a table
 __global__ void k_win64(const double* __restrict__ frac, int64_t M, int dims, int m, double beta,
