@@ -597,6 +597,332 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
   for (int i = threadIdx.x; i < PART / 2; i += blockDim.x) out[i] = src[i];
 }
 
+// ---------------------------------------------------------------- tensor-core interpolation
+// float32, W = 8 taps, 2b = 8 boundary columns, 16 x 16 tiles.  With the staged
+// grid tile G[x][y], side segments S0[k][y], S1[k][x] and corner coefficients
+// X[ky][kx] of one work item, a batch of 32 samples needs
+//   H[s][x]  = sum_y wy_s[y - py_s] G[x][y]        (interior, then sum_a wx_s[a] H[s][px_s + a])
+//   Q0[s][k] = sum_y wy_s[y - py_s] S0[k][y]       (x-sides, then sum_k bx_s[k] Q0[s][k])
+//   Q1[s][k] = sum_x wx_s[x - px_s] S1[k][x]       (y-sides, then sum_k by_s[k] Q1[s][k])
+//   RR[s][ky] = sum_kx bx_s[kx] X[ky][kx]          (corners, then sum_ky by_s[ky] RR[s][ky])
+// i.e. GEMMs with M = samples, on mma.sync m16n8k8 TF32 with the 3xTF32 split.
+// The window operand is never written out: a lane's fragment rows are fixed
+// samples, and its element (row s, column k0 + c) is tap k0 + c - pos_s of s,
+// nonzero in exactly one of the three k-steps; each lane loads and splits its
+// taps once per batch and selects them per step.  The item operands G, S0, S1
+// are split once per item into (hi, lo) pairs.  Per batch: cp.async stages the
+// next batch's inputs; warps 0-1 form H (one 16-sample block each, real and
+// imaginary part), warp 2 Q0 and half of RR, warp 3 Q1 and the other half; then
+// four threads per sample combine
+//   y = wx wy sum_a wx_a H[px + a] + wy sum_k bx_k Q0_k + wx sum_k by_k Q1_k + sum_k by_k RR_k.
+namespace tci {
+using tc::split;
+using tc::mma;
+using tc::cp_async16;
+using tc::cp_async8;
+using tc::cp_async4;
+using tc::cp_commit;
+using tc::cp_wait_all;
+constexpr int SBT = 32, W = 8, B2 = 8, TILE = 16, PW = TILE + W;
+constexpr int LDP = 28;  // rows of the (hi, lo) item operands [n][k] in pairs: conflict-free 64-bit fragments
+constexpr int LDX = 20;  // rows of the corner operands (K = 16), stored [ky][k]
+constexpr int LDS = 20;  // staged rows of 16 floats
+constexpr int LDH = 56;  // H rows: 24 complex + pad (floats)
+constexpr int LDQ = 18;  // Q0, Q1, RR rows: 8 complex + pad (floats)
+// item operands (floats; the paired planes hold float2 (hi, lo) per element)
+constexpr int I_GR = 0, I_GI = I_GR + 2 * PW * LDP;  // [x][y]
+constexpr int I_S0R = I_GI + 2 * PW * LDP, I_S0I = I_S0R + 2 * B2 * LDP;  // [k][y]
+constexpr int I_S1R = I_S0I + 2 * B2 * LDP, I_S1I = I_S1R + 2 * B2 * LDP;  // [k][x]
+constexpr int I_XR = I_S1I + 2 * B2 * LDP;  // [ky][k]: k < 8 Re X[ky][k], k >= 8 -Im X[ky][k - 8]
+constexpr int I_XI = I_XR + B2 * LDX;       // [ky][k]: k < 8 Im X[ky][k], k >= 8  Re X[ky][k - 8]
+constexpr int N_ITEM = I_XI + B2 * LDX;
+// products of the batch
+constexpr int O_H = N_ITEM, O_Q0 = O_H + SBT * LDH, O_Q1 = O_Q0 + SBT * LDQ, O_RR = O_Q1 + SBT * LDQ;
+// staged inputs, two buffers: taps wx | wy, bx, by (complex), phases wx wy, grid indices
+constexpr int ST_WIN = 0, ST_BX = ST_WIN + SBT * LDS, ST_BY = ST_BX + SBT * LDS, ST_W = ST_BY + SBT * LDS;
+constexpr int ST_FL = ST_W + 4 * SBT;
+constexpr int ST_SIZE = ST_FL + 2 * SBT;
+constexpr int S_STAGE = O_RR + SBT * LDQ;
+constexpr int N_SMEM = S_STAGE + 2 * ST_SIZE;
+static_assert(S_STAGE % 4 == 0 && ST_SIZE % 4 == 0 && O_H % 2 == 0, "16-byte staging, 8-byte products");
+
+__device__ inline void stage(float* st, int wid, int lane, int sb, int nb, const float* __restrict__ win,
+                             const float2* __restrict__ w, const float2* __restrict__ bf,
+                             const int32_t* __restrict__ fl, int64_t M) {
+  if (lane >= nb) return;
+  const int64_t s = sb + lane;
+  if (wid == 0) {
+    const float* src = win + s * (2 * W);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cp_async16(st + ST_WIN + lane * LDS + 4 * c, src + 4 * c);
+  } else if (wid < 3) {
+    const float2* src = bf + (s + (wid == 2 ? M : 0)) * B2;
+    float* dst = st + (wid == 1 ? ST_BX : ST_BY) + lane * LDS;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) cp_async16(dst + 4 * c, src + 2 * c);
+  } else {
+    cp_async8(st + ST_W + 4 * lane, w + s);
+    cp_async8(st + ST_W + 4 * lane + 2, w + M + s);
+    cp_async4(st + ST_FL + 2 * lane, fl + s);
+    cp_async4(st + ST_FL + 2 * lane + 1, fl + M + s);
+  }
+}
+// The lane's window elements of one batch: for fragment rows h (samples rs0 + g +
+// 8h, window start pos[h]; pos < -W for an empty row) and column halves e
+// (columns t + 4e + 8 step), the step at which tap t + 4e + 8 step - pos is in
+// range and that tap, split
+template <int NH>
+__device__ inline void win_elems(const float* taps, const int* pos, int rs0, int lane, int* ks, uint32_t* hi,
+                                 uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int h = 0; h < NH; ++h)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int c0 = t + 4 * e - pos[h];      // column offset at step 0, in [-15, 7] or >= 16
+      const int step = (7 - c0) >> 3;         // 0..2 for a sample, negative for an empty row
+      float v = 0.0f;
+      if (step >= 0) v = taps[(rs0 + g + 8 * (h & 1) + 16 * (h >> 1)) * LDS + c0 + 8 * step];
+      ks[2 * h + e] = step;
+      split(v, hi[2 * h + e], lo[2 * h + e]);
+    }
+}
+// B fragment (8 x 8) of a paired [n][k] operand
+__device__ inline void frag_b_pair(const float* B, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
+  const int g = lane >> 2, t = lane & 3;
+  const float2 p0 = *reinterpret_cast<const float2*>(B + 2 * ((n0 + g) * LDP + k0 + t));
+  const float2 p1 = *reinterpret_cast<const float2*>(B + 2 * ((n0 + g) * LDP + k0 + t + 4));
+  hi[0] = __float_as_uint(p0.x);
+  lo[0] = __float_as_uint(p0.y);
+  hi[1] = __float_as_uint(p1.x);
+  lo[1] = __float_as_uint(p1.y);
+}
+__device__ inline void put_pair(float* B, int r, int c, float v) {
+  uint32_t h, l;
+  split(v, h, l);
+  *reinterpret_cast<float2*>(B + 2 * (r * LDP + c)) = make_float2(__uint_as_float(h), __uint_as_float(l));
+}
+}  // namespace tci
+
+static __global__ void __launch_bounds__(128, 4) k_interp2d_tc(
+    const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl,
+    const float* __restrict__ win, const float2* __restrict__ w, const float2* __restrict__ bf,
+    const float2* __restrict__ grid, const float2* __restrict__ hbuf, const float2* __restrict__ side, int n,
+    const float2* __restrict__ x, int N, int64_t M, int nbx, const int32_t* __restrict__ perm,
+    float2* __restrict__ y, double* __restrict__ norm_part) {
+  using namespace tci;
+  extern __shared__ __align__(16) float sm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int it = order[blockIdx.x];  // work item (larger items launch first)
+  const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
+  const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
+  constexpr int m = W / 2, b = B2 / 2;
+  const int nm = n - 1, gx0 = ox - m + 1, gy0 = oy - m + 1;
+  stage(sm + S_STAGE, wid, lane, s0, min(SBT, s1 - s0), win, w, bf, fl, M);
+  cp_commit();
+  // item operands (staged row i <-> grid point o - m + 1 + i)
+  for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
+    const int r = i / PW, c = i - r * PW;
+    const float2 v = grid[(int64_t)((gx0 + r) & nm) * n + ((gy0 + c) & nm)];
+    put_pair(sm + I_GR, r, c, v.x);
+    put_pair(sm + I_GI, r, c, v.y);
+  }
+  for (int i = threadIdx.x; i < B2 * PW; i += blockDim.x) {
+    const int k = i / PW, c = i - k * PW;
+    const float2 a = side[(int64_t)k * n + ((gy0 + c) & nm)];
+    const float2 e = hbuf[(int64_t)bcol(k, b, N) * n + ((gx0 + c) & nm)];
+    put_pair(sm + I_S0R, k, c, a.x);
+    put_pair(sm + I_S0I, k, c, a.y);
+    put_pair(sm + I_S1R, k, c, e.x);
+    put_pair(sm + I_S1I, k, c, e.y);
+  }
+  if (threadIdx.x < B2 * B2) {
+    const int kx = threadIdx.x % B2, ky = threadIdx.x / B2;
+    const float2 X = x[(int64_t)bcol(ky, b, N) * N + bcol(kx, b, N)];
+    sm[I_XR + ky * LDX + kx] = X.x;
+    sm[I_XR + ky * LDX + B2 + kx] = -X.y;
+    sm[I_XI + ky * LDX + kx] = X.y;
+    sm[I_XI + ky * LDX + B2 + kx] = X.x;
+  }
+  const int ps = threadIdx.x >> 2, pq = threadIdx.x & 3;  // combine step: sample, term
+  double nacc = 0.0;
+  int buf = 0;
+  for (int sb = s0; sb < s1; sb += SBT, buf ^= 1) {
+    const int nb = min(SBT, s1 - sb);
+    cp_wait_all();
+    __syncthreads();  // this batch staged, item operands written; the last combine step done
+    if (sb + SBT < s1)
+      stage(sm + S_STAGE + (buf ^ 1) * ST_SIZE, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, fl, M);
+    cp_commit();
+    const float* st = sm + S_STAGE + buf * ST_SIZE;
+    const int* sfl = reinterpret_cast<const int*>(st + ST_FL);
+    float acc[6][4];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][q] = 0.0f;
+    if (wid < 2) {
+      // H for samples m0 .. m0+15: tiles [re: 0-2 | im: 3-5][x block]
+      const int m0 = 16 * wid;
+      int pos[2], ks[4];
+      uint32_t th[4], tl[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int s = m0 + g + 8 * h;
+        pos[h] = (s < nb) ? sfl[2 * s + 1] - oy : -2 * W;
+      }
+      win_elems<2>(st + ST_WIN + W, pos, m0, lane, ks, th, tl);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uint32_t ah[4], al[4], bh[2][3][2], bl[2][3][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {  // fragment element q = row half + 2 column half
+          const int i = 2 * (q & 1) + (q >> 1);
+          ah[q] = (ks[i] == k) ? th[i] : 0u;
+          al[q] = (ks[i] == k) ? tl[i] : 0u;
+        }
+#pragma unroll
+        for (int nbk = 0; nbk < 3; ++nbk) {
+          frag_b_pair(sm + I_GR, 8 * nbk, 8 * k, lane, bh[0][nbk], bl[0][nbk]);
+          frag_b_pair(sm + I_GI, 8 * nbk, 8 * k, lane, bh[1][nbk], bl[1][nbk]);
+        }
+#pragma unroll
+        for (int term = 0; term < 3; ++term)
+#pragma unroll
+          for (int nbk = 0; nbk < 3; ++nbk)
+#pragma unroll
+            for (int ri = 0; ri < 2; ++ri)
+              mma(acc[3 * ri + nbk], term == 2 ? al : ah, term == 1 ? bl[ri][nbk] : bh[ri][nbk]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = m0 + g + ((q & 2) ? 8 : 0);
+#pragma unroll
+        for (int nbk = 0; nbk < 3; ++nbk) {
+          const int c = 8 * nbk + 2 * t + (q & 1);
+          *reinterpret_cast<float2*>(sm + O_H + r * LDH + 2 * c) = make_float2(acc[nbk][q], acc[3 + nbk][q]);
+        }
+      }
+    } else {
+      // warp 2: Q0 (wy, S0), warp 3: Q1 (wx, S1); tiles [block][re | im]; corners in 4, 5
+      const bool xs = (wid == 2);
+      int pos[4], ks[8];
+      uint32_t th[8], tl[8];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int s = g + 8 * h;
+        pos[h] = (s < nb) ? sfl[2 * s + (xs ? 1 : 0)] - (xs ? oy : ox) : -2 * W;
+      }
+      win_elems<4>(st + ST_WIN + (xs ? W : 0), pos, 0, lane, ks, th, tl);
+      const float* Sr = sm + (xs ? I_S0R : I_S1R);
+      const float* Si = sm + (xs ? I_S0I : I_S1I);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        uint32_t ah[2][4], al[2][4], bh[2][2], bl[2][2];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = 2 * (2 * mb + (q & 1)) + (q >> 1);
+            ah[mb][q] = (ks[i] == k) ? th[i] : 0u;
+            al[mb][q] = (ks[i] == k) ? tl[i] : 0u;
+          }
+        frag_b_pair(Sr, 0, 8 * k, lane, bh[0], bl[0]);
+        frag_b_pair(Si, 0, 8 * k, lane, bh[1], bl[1]);
+#pragma unroll
+        for (int term = 0; term < 3; ++term)
+#pragma unroll
+          for (int tq = 0; tq < 4; ++tq)
+            mma(acc[tq], term == 2 ? al[tq >> 1] : ah[tq >> 1], term == 1 ? bl[tq & 1] : bh[tq & 1]);
+      }
+      // corners for samples rc .. rc+15: A = [Re bx | Im bx], K = 16
+      const int rc = xs ? 0 : 16;
+#pragma unroll
+      for (int k0 = 0; k0 < 2 * B2; k0 += 8) {
+        uint32_t ah[4], al[4], bh[2][2], bl[2][2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int s = rc + g + 8 * h, kk = k0 + t + 4 * e;
+            const float v = (s < nb) ? st[ST_BX + s * LDS + 2 * (kk & 7) + (kk >> 3)] : 0.0f;
+            split(v, ah[h + 2 * e], al[h + 2 * e]);
+          }
+        tc::load_bT(sm + I_XR, LDX, 0, k0, lane, bh[0], bl[0]);
+        tc::load_bT(sm + I_XI, LDX, 0, k0, lane, bh[1], bl[1]);
+#pragma unroll
+        for (int term = 0; term < 3; ++term)
+#pragma unroll
+          for (int ri = 0; ri < 2; ++ri) mma(acc[4 + ri], term == 2 ? al : ah, term == 1 ? bl[ri] : bh[ri]);
+      }
+      float* Q = sm + (xs ? O_Q0 : O_Q1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = g + ((q & 2) ? 8 : 0), c = 2 * t + (q & 1);
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+          *reinterpret_cast<float2*>(Q + (16 * mb + r) * LDQ + 2 * c) = make_float2(acc[2 * mb][q], acc[2 * mb + 1][q]);
+        *reinterpret_cast<float2*>(sm + O_RR + (rc + r) * LDQ + 2 * c) = make_float2(acc[4][q], acc[5][q]);
+      }
+    }
+    __syncthreads();  // products complete
+    {
+      float2 c = make_float2(0.0f, 0.0f);
+      const int j = ps;
+      if (j < nb) {
+        const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * j);
+        const float2 wxs = make_float2(ww.x, ww.y), wys = make_float2(ww.z, ww.w);
+        if (pq == 0) {  // interior
+          const int px = sfl[2 * j] - ox;
+          const float* tp = st + ST_WIN + j * LDS;
+          const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
+          const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+          const float2* hr = reinterpret_cast<const float2*>(sm + O_H + j * LDH) + px;
+          float2 vi = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int a = 0; a < W; ++a) {
+            const float2 hv = hr[a];
+            vi.x += tap[a] * hv.x;
+            vi.y += tap[a] * hv.y;
+          }
+          c = cmul(cmul(wxs, wys), vi);
+        } else {  // 1: x-sides with bx, 2: y-sides with by, 3: corners with by
+          const float* bp = st + (pq == 1 ? ST_BX : ST_BY) + j * LDS;
+          const float2* qr = reinterpret_cast<const float2*>(sm + (pq == 1 ? O_Q0 : pq == 2 ? O_Q1 : O_RR) + j * LDQ);
+          float2 sacc = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float4 f = *reinterpret_cast<const float4*>(bp + 4 * h);
+            sacc = cadd(sacc, cmul(make_float2(f.x, f.y), qr[2 * h]));
+            sacc = cadd(sacc, cmul(make_float2(f.z, f.w), qr[2 * h + 1]));
+          }
+          c = (pq == 1) ? cmul(wys, sacc) : (pq == 2) ? cmul(wxs, sacc) : sacc;
+        }
+      }
+      // (c0 + c1) + (c2 + c3) in every lane of the sample's group
+      c.x += __shfl_xor_sync(0xffffffffu, c.x, 1);
+      c.y += __shfl_xor_sync(0xffffffffu, c.y, 1);
+      c.x += __shfl_xor_sync(0xffffffffu, c.x, 2);
+      c.y += __shfl_xor_sync(0xffffffffu, c.y, 2);
+      if (pq == 0 && j < nb) {
+        const int s = sb + j;
+        y[perm ? perm[s] : s] = c;
+        nacc += (double)c.x * c.x + (double)c.y * c.y;
+      }
+    }
+  }
+  if (norm_part) {  // ||y||^2 over this item's samples: lanes, then warps, in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+    __syncthreads();  // the products are no longer read
+    double* wsum = reinterpret_cast<double*>(sm + O_H);
+    if (lane == 0) wsum[wid] = nacc;
+    __syncthreads();
+    if (threadIdx.x == 0) norm_part[it] = ((wsum[0] + wsum[1]) + wsum[2]) + wsum[3];
+  }
+}
+
 template <typename R>
 gs_status set_smem_attr(const void* fn, size_t bytes) {
   if (bytes > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -634,6 +960,18 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
     constexpr int W = decltype(wc)::value;
     constexpr int B2 = decltype(bc)::value;
     const int PW = tile + W;
+    if (sizeof(R) == 4 && W == 8 && B2 == 8 && tile == 16 && !std::getenv("GS_NO_TC")) {
+      const size_t shc = (size_t)tci::N_SMEM * sizeof(float);
+      gs_status e = set_smem_attr<R>((const void*)k_interp2d_tc, shc);
+      if (e != GS_OK) return e;
+      GS_LAUNCH("interp2d<f32>", st,
+                k_interp2d_tc<<<P->nwork, 128, shc, st>>>(
+                    P->work, P->work_order, P->fl, (const float*)D.win, (const float2*)D.w, (const float2*)D.bf,
+                    (const float2*)D.grid, (const float2*)D.hbuf, (const float2*)D.side, (int)P->n,
+                    (const float2*)x, (int)P->N, P->M, P->nbx, perm, (float2*)y, norm_part));
+      GS_CUDA(cudaGetLastError());
+      return GS_OK;
+    }
     const size_t sh = ((size_t)PW * PW + 2 * (size_t)b2 * PW + (size_t)b2 * b2) * sizeof(C<R>);
     gs_status e = set_smem_attr<R>((const void*)k_interp2d<R, W, B2>, sh);
     if (e != GS_OK) return e;

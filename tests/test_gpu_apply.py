@@ -141,3 +141,34 @@ def test_adjoint_identity_on_gpu():
         Thy = plan.TH(dev(y, prec), prec).cpu().numpy().astype(np.complex128)
         a, b = np.vdot(y, Tx), np.vdot(Thy, x)
         assert abs(a - b) / abs(a) < tol
+
+
+def test_2d_tensor_core_and_scalar_paths(monkeypatch):
+    """db4, float32, 16 x 16 tiles: the tensor-core interpolation and spread
+    (3xTF32) and the scalar kernels (GS_NO_TC=1) both meet the float32 tolerance
+    against the oracle, on work items from 1 to 512 samples (dense centre,
+    sparse rim, ragged last batches)."""
+    g = synth.rng(14)
+    J = 6
+    xi2 = np.concatenate([g.normal(0, 3.0, size=(9000, 2)), g.uniform(-64, 64, size=(1237, 2))])
+    M = xi2.shape[0]
+    op = Operator2D(Basis1D(4, J), xi2)
+    plan = gs.Plan.plan_2d(xi2, 4, J, direct=0)
+    x = rand_c(g, 4**J)
+    y = rand_c(g, M)
+    ref_T, ref_TH = op.apply(x), op.adjoint(y)
+    tol = tol_for(gs.GS_FP32, 2 * 2**J)
+    out = {}
+    for no_tc in (False, True):
+        if no_tc:
+            monkeypatch.setenv("GS_NO_TC", "1")
+        else:
+            monkeypatch.delenv("GS_NO_TC", raising=False)
+        yg = plan.T(dev(x, gs.GS_FP32), gs.GS_FP32).cpu().numpy()
+        zg = plan.TH(dev(y, gs.GS_FP32), gs.GS_FP32).cpu().numpy()
+        assert rel(yg, ref_T) < tol, (no_tc, rel(yg, ref_T))
+        assert rel(zg, ref_TH) < tol, (no_tc, rel(zg, ref_TH))
+        out[no_tc] = (yg, zg)
+    # the two float32 evaluations differ only by rounding
+    assert rel(out[False][0], out[True][0]) < tol
+    assert rel(out[False][1], out[True][1]) < tol
