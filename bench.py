@@ -111,19 +111,34 @@ def workload():
 # bytes one launch of each kernel must move (tables it streams + its input and
 # output vectors; the oversampled grids are method-internal and not counted)
 def kernel_bytes(name, M, N, b, m_lo=4, m_hi=8):
-    """Bytes per launch: per sample the grid cell (2 int32), the float32 window
-    table (2 x 2m float) or, in float64, the fractional coordinates (2 double),
-    the interior factors (2 complex) and the boundary factors (2 x 2b complex),
-    plus the sample value read or written; the corner coefficients once."""
+    """Algorithmic bytes of one launch of a per-sample 2D kernel, by the byte model
+    of the method's representation: per sample the interior factors phi-hat_x,
+    phi-hat_y (2 complex), the boundary factors L_x, R_x, L_y, R_y (4b complex),
+    the sample value (1 complex) and xi_x, xi_y, sqrt(mu) (3 reals): 164 B in
+    float32, 328 B in float64.  The oversampled grid is method-internal."""
+    f32 = "<f32>" in name
+    sc, sr = (8, 4) if f32 else (16, 8)
+    if name.startswith("interp2d") or name.startswith("spread2d"):
+        return M * (sc * (2 + 4 * b + 1) + sr * 3)
+    return None
+
+
+def streamed_bytes(name, M, b, m_lo=4):
+    """Bytes the kernel actually streams per launch in this implementation: per
+    sample the grid cell (2 int32), the precomputed float32 window values (2 x 2m)
+    or float64 fractional coordinates, the interior and boundary factors and the
+    sample value (more than kernel_bytes: window values replace xi)."""
     f32 = "<f32>" in name
     sc = 8 if f32 else 16
     coord = 2 * (2 * m_lo) * 4 if f32 else 2 * 8
-    per_sample = 2 * 4 + coord + 2 * sc + 2 * (2 * b) * sc
-    if name.startswith("interp2d"):
-        return M * (per_sample + sc) + (2 * b) ** 2 * sc
-    if name.startswith("spread2d"):
-        return M * (per_sample + sc)
-    return None
+    return M * (2 * 4 + coord + 2 * sc + 2 * (2 * b) * sc + sc)
+
+
+def apply_bytes(M, N, b, f32=True):
+    """Algorithmic bytes of one 2D apply (T or T^H): the coefficient vector (N^2
+    complex) plus the per-sample tables of kernel_bytes."""
+    sc, sr = (8, 4) if f32 else (16, 8)
+    return sc * (N * N + M * (2 + 4 * b) + M) + sr * 3 * M
 
 
 # ------------------------------------------------------------------ oracle baseline
@@ -280,11 +295,15 @@ def main():
     roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else
-                "fallback 6.8 TB/s", "bytes_per_launch": bytes_launch, "avg_launch_us": avg_s * 1e6,
+                "fallback 6.8 TB/s", "bytes_per_launch": bytes_launch,
+                "bytes_model": "164 B per sample (float32): phi-hat x/y, 4b boundary factors, sample value, "
+                               "xi x/y, sqrt(mu)",
+                "streamed_bytes_per_launch": streamed_bytes(name, M, b), "avg_launch_us": avg_s * 1e6,
                 "launches": cnt, "share_of_step": ms / prof_total,
                 "note": "per-launch CUDA events over a second identical pass of the timed steps; tables are "
                         "L2-resident across the CGLS iterations of one reconstruction"}
     shares = {k: round(v[1] / prof_total, 4) for k, v in ranked[:12]}
+    apply = apply_timings(gs, plan, flush, M, 2**J, b, peak)
 
     # ---- plain float64 CGLS on the same problem (the spec comparison)
     fp64 = None
@@ -324,7 +343,7 @@ def main():
                    "parallelism": f"{world} independent GPU(s)", "init_ms": init_ms},
         "iterations": iters, "converged": ok, "rel_normres": [i["rel_normres"] for i in infos],
         "outer": [i["outer"] for i in infos],
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "kernel_shares": shares,
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "apply": apply, "kernel_shares": shares,
         "fp64_cgls": fp64, "batch": batch, "learned": learned, "cpu_baseline": cpu, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -447,6 +466,48 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
             "loss_first": losses[0], "loss_last": float(np.mean(losses[-max(1, ntrain // batch):])),
             "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ,
             "net": "6 conv3x3 layers 2-32-32-32-32-32-2, ReLU, residual, bf16 inference weights"}
+
+
+def apply_timings(gs, plan, flush, M, N, b, peak, reps=20):
+    """float32 T and T^H applies through the public API (caller's sample order):
+    warm = `reps` back-to-back applies, cold = L2 flushed before each (median);
+    GB/s of the apply's algorithmic bytes (apply_bytes)."""
+    import torch
+
+    g = np.random.default_rng(0)
+    y = torch.tensor(g.standard_normal(M) + 1j * g.standard_normal(M), dtype=torch.complex64, device="cuda")
+    x = torch.tensor(g.standard_normal(plan.ncoef) + 1j * g.standard_normal(plan.ncoef), dtype=torch.complex64,
+                     device="cuda")
+    z, q = torch.empty_like(x), torch.empty_like(y)
+    fns = {"T": lambda: gs.gs_apply_T(plan.handle, gs.GS_FP32, x, q),
+           "TH": lambda: gs.gs_apply_TH(plan.handle, gs.GS_FP32, y, z)}
+    B = apply_bytes(M, N, b)
+    out = {"bytes_per_apply": B, "unit": "GB/s", "peak": peak,
+           "note": "float32 applies, user sample order; warm: back to back, cold: L2 flushed before each"}
+    for name, fn in fns.items():
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        warm_us = e0.elapsed_time(e1) * 1e3 / reps
+        cold = []
+        for _ in range(reps):
+            flush.zero_()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            cold.append(e0.elapsed_time(e1) * 1e3)
+        cold_us = float(np.median(cold))
+        out[name] = {"warm_us": warm_us, "cold_us": cold_us, "warm_gbs": B / warm_us / 1e3,
+                     "cold_gbs": B / cold_us / 1e3, "warm_frac": B / warm_us / 1e3 / peak,
+                     "cold_frac": B / cold_us / 1e3 / peak}
+    return out
 
 
 def probe_apply(reps):
