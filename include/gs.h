@@ -130,7 +130,8 @@ typedef struct {
                      ||T^H y|| (else the solve starts from x = 0); 0: start from x = 0 [0] */
   int max_outer;  /* refinement passes in GS_SOLVE_MIXED [8] */
   double inner_rtol; /* GS_SOLVE_MIXED: a pass stops when its ||T^H (r - T d)|| falls
-                        by this factor (or below tol ||T^H y|| / 2); 0 = default [1e-4] */
+                        by this factor (or below tol ||T^H y|| / 2); 0 = default
+                        [min(1e-4, 0.3 tol) for tol >= 1e-6, else 1e-4] */
 } gs_solve_opts;
 
 typedef struct {

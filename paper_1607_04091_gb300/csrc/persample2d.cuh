@@ -307,7 +307,9 @@ __global__ void __launch_bounds__(256) k_spread2d(
 namespace tc {
 constexpr int SBT = 32;  // samples per batch (the K of one round)
 constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
-constexpr int LDO = 40;  // rows of the 32-wide operands (conflict-free fragments)
+constexpr int LDO = 24;  // rows of the window operands: 24 grid offsets (conflict-free fragments);
+                         // the second 16-row block reads 8 entries past a row (the next row's),
+                         // which only reach output rows >= 24, never stored
 constexpr int LDT = 36;  // boundary operands stored transposed, [k][sample]: conflict-free
                          // writes (one lane per sample) and fragment loads
 constexpr int LDS = 20;  // staged rows of 16 floats (conflict-free float4 reads)
