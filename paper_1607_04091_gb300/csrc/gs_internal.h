@@ -175,8 +175,23 @@ gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStrea
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
                  double* norm_part = nullptr);
+// The vector update of a CG step fused into the adjoint's last pass (2D plans):
+// after z = T^H q, x += alpha p and s -= alpha z over all coefficients, with the
+// per-CTA partial sums of the new ||s||^2 in part (one per coefficient row, N
+// values); skipped while flag[0] != 0.  join_branch >= 0: side branch to join
+// before that pass (where alpha is computed).
+template <typename R> struct CgStep {
+  C<R>* x;
+  const C<R>* p;
+  C<R>* s;
+  const double* alpha;
+  const int* flag;
+  double* part;
+  int join_branch;
+};
 template <typename R>
-gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st);
+gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,
+                  const CgStep<R>* cg = nullptr);
 template <typename R>
 gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
                           cudaStream_t st);

@@ -665,7 +665,7 @@ template <typename R>
 __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restrict__ side1,
                               const C<R>* __restrict__ corner, const R* __restrict__ deap, int N,
                               int n, int logn, int b, int rows, const C<R>* __restrict__ tw,
-                              C<R>* __restrict__ z) {
+                              C<R>* __restrict__ z, CgStep<R> cg) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int j0 = blockIdx.x * rows;
@@ -696,6 +696,35 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
       [&](int t, Cv<R> o) {
         if (o.ok) z[(int64_t)(j0 + t / N) * N + t % N] = o.v;
       });
+  if (cg.x) {  // fused CG update of rows j0 .. j0+nr-1 (their x-side entries came from pass 2)
+    __shared__ int run;
+    __shared__ double wsum[32];
+    if (threadIdx.x == 0) run = (cg.flag[0] == 0);
+    __syncthreads();  // also orders this CTA's z stores before the reads below
+    if (!run) return;
+    const R a = (R)cg.alpha[0];
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
+      const int64_t k = (int64_t)j0 * N + t;
+      C<R> xv = cg.x[k], pv = cg.p[k], sv = cg.s[k], zv = z[k];
+      xv.x += a * pv.x;
+      xv.y += a * pv.y;
+      sv.x -= a * zv.x;
+      sv.y -= a * zv.y;
+      cg.x[k] = xv;
+      cg.s[k] = sv;
+      acc += (double)sv.x * sv.x + (double)sv.y * sv.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tsum = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[w];
+      cg.part[blockIdx.x] = tsum;
+    }
+  }
 }
 
 template <typename R>
@@ -769,7 +798,8 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
 }
 
 template <typename R>
-gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st) {
+gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,
+                  const CgStep<R>* cg) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
   const int64_t M = P->M;
   const R beta = (R)D.beta;
@@ -848,10 +878,12 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
+    if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
+    const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
               k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
-                                                                         D.tw, z));
+                                                                         D.tw, z, cgv));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -928,7 +960,9 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
               k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
-                                                                         D.tw, z));
+                                                                         D.tw, z, CgStep<R>{nullptr, nullptr, nullptr,
+                                                                                            nullptr, nullptr, nullptr,
+                                                                                            -1}));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -951,9 +985,10 @@ template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*
                                  double*);
 template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t,
                                   double*);
-template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t);
+template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
+                                  const CgStep<float>*);
 template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,
-                                   cudaStream_t);
+                                   cudaStream_t, const CgStep<double>*);
 template gs_status nfft_TH_scratch<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, float2*,
                                           cudaStream_t);
 template gs_status nfft_TH_scratch<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,

@@ -246,17 +246,25 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
   // ||s||^2 partials go after the ||q||^2 ones
   double* red_s = P->red + std::max<int64_t>(P->nwork, RED_BLOCKS);
   const int gs = grid_for(nc);
+  int np_s = gs;  // number of ||s||^2 partials
   if (normal_eq) {
     // alpha on a side branch: only the update after T^H q needs it
     GS_TRY(fork_aux(P, st, 2));
     cudaStream_t a2 = side_stream(P, st, 2);
     GS_LAUNCH("cgls_scalar", a2, k_alpha<<<1, 256, 0, a2>>>(P->red, np, P->scal, P->flag));
     GS_CUDA(cudaGetLastError());
-    s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
-    if (s != GS_OK) return s;
-    GS_TRY(join_aux(P, st, 2));
-    GS_LAUNCH("cgls_axpy", st,
-              k_update_xs<R><<<gs, 256, 0, st>>>(D.vx, D.vp, D.vs, D.vz, nc, P->scal, P->flag, red_s));
+    if (!P->direct && P->dims == 2) {
+      // 2D: the x and s update runs in the adjoint's last pass, one partial per coefficient row
+      const CgStep<R> cg{D.vx, D.vp, D.vs, P->scal + S_ALPHA, P->flag, red_s, 2};
+      GS_TRY(nfft_TH<R>(P, D, D.vq, D.vz, nullptr, st, &cg));
+      np_s = (int)P->N;
+    } else {
+      s = apply_TH<R>(P, D, D.vq, D.vz, nullptr, st);
+      if (s != GS_OK) return s;
+      GS_TRY(join_aux(P, st, 2));
+      GS_LAUNCH("cgls_axpy", st,
+                k_update_xs<R><<<gs, 256, 0, st>>>(D.vx, D.vp, D.vs, D.vz, nc, P->scal, P->flag, red_s));
+    }
   } else {
     GS_LAUNCH("cgls_scalar", st, k_alpha<<<1, 256, 0, st>>>(P->red, np, P->scal, P->flag));
     GS_LAUNCH("cgls_axpy", st,
@@ -265,7 +273,7 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
     if (s != GS_OK) return s;
     GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<gs, 256, 0, st>>>(D.vs, nc, red_s, P->flag));
   }
-  GS_LAUNCH("cgls_scalar", st, k_beta_p<R><<<gs, 256, 0, st>>>(red_s, gs, D.vp, D.vs, nc, P->scal, P->flag));
+  GS_LAUNCH("cgls_scalar", st, k_beta_p<R><<<gs, 256, 0, st>>>(red_s, np_s, D.vp, D.vs, nc, P->scal, P->flag));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
