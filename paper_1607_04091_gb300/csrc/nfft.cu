@@ -41,7 +41,8 @@ using namespace dev;
 // takes the R-point DFT in registers and writes it to (j div Ns) Ns R + (j mod Ns)
 // + r Ns.  Every thread holds PPT points per pass (the caller launches at least
 // nb n / PPT threads); a pass is load, barrier, compute and store, barrier.
-// Twiddles from the plan's table: tw[k tws] = e^{-2 pi i k / n}, k < n/2.
+// Twiddles: the base e^{-+2 pi i (j mod Ns) / (Ns R)} from the plan's table
+// tw[k tws] = e^{-2 pi i k / n}, k < n/2, and its powers by multiplication.
 template <typename R> __device__ inline C<R> csub(C<R> a, C<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
 // a (-i), or a i for the inverse
 template <typename R> __device__ inline C<R> rot_q(C<R> a, bool inv) { return inv ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x); }
@@ -101,22 +102,31 @@ __device__ inline void fft_pass(C<R>* buf, int nb, int n, int lgq, int lgNs, con
       for (int r = 0; r < RAD; ++r) v[k][r] = src[r * q];
     }
   }
+  // base twiddle e^{-+2 pi i jm / (Ns RAD)} = table entry jm (n / (Ns RAD)) tws (below n tws / 2);
+  // it does not depend on the data, so its load overlaps the barrier
+  C<R> wb[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const int bi = threadIdx.x + k * blockDim.x;
+    wb[k] = mk<R>(1, 0);
+    if (bi < nbf && lgNs > 0) {
+      const int jm = (bi & (q - 1)) & (Ns - 1);
+      wb[k] = tw[(jm << (lgq - lgNs)) * tws];
+      if (inv) wb[k].y = -wb[k].y;
+    }
+  }
   __syncthreads();
-  const int half = (n * tws) >> 1;
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     const int bi = threadIdx.x + k * blockDim.x;
     if (bi < nbf) {
       const int row = bi >> lgq, j = bi & (q - 1), jm = j & (Ns - 1);
-      if (lgNs > 0) {
-        // e^{-+2 pi i r jm / (Ns RAD)} = table entry r jm (n / (Ns RAD)) tws, below n tws
-        const int step = (jm << (lgq - lgNs)) * tws;
+      if (lgNs > 0) {  // twiddle r = base^r (rounding error <= r ulp)
+        C<R> w = wb[k];
+        v[k][1] = cmul(v[k][1], w);
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-          const int e = r * step;
-          C<R> w = (e < half) ? tw[e] : tw[e - half];
-          if (e >= half) w = mk<R>(-w.x, -w.y);
-          if (inv) w.y = -w.y;
+        for (int r = 2; r < RAD; ++r) {
+          w = cmul(w, wb[k]);
           v[k][r] = cmul(v[k][r], w);
         }
       }

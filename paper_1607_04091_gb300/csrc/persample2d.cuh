@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(256) k_spread2d(
 //   S1[k][x]  += v1_s[k] wx_s[x - px_s]                    y-sides,  v1 = u conj(wx) conj(by_k)
 //   Cc[kx][ky]+= A_s[kx] conj(by_s[ky])                     corners,  A = u conj(bx)
 // i.e. GEMMs with K = samples.  The samples go in batches of 32:
-//   staging  cp.async copies the batch's per-sample inputs (taps, boundary
-//            factors, phases, u, grid indices) to shared memory while the
-//            previous batch is multiplied;
+//   staging  cp.async copies the next batch's per-sample inputs (taps,
+//            boundary factors, phases, u, grid indices) to the other of two
+//            shared-memory buffers while this batch is built and multiplied;
 //   phase 1  warp q writes operand q (v wx re, v wx im, wx, wy as rows of 32
 //            grid offsets, zero outside the sample's 8 taps) and two boundary
 //            operands, one lane per sample;
@@ -319,12 +319,15 @@ constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + B2 * LDT, O_V1R = O_V0I 
 constexpr int O_V1I = O_V1R + B2 * LDT, O_CR = O_V1I + B2 * LDT, O_CI = O_CR + B2 * LDT;
 constexpr int O_K = O_CI + B2 * LDT;  // [Re A_0..7 | Im A_0..7][sample]
 constexpr int N_OPER = O_K + 2 * B2 * LDT;
-// staging area (floats, after the operands)
-constexpr int S_WIN = N_OPER, S_BX = S_WIN + SBT * LDS, S_BY = S_BX + SBT * LDS;
+// staging, two buffers after the operands (offsets within a buffer, floats)
+constexpr int S_WIN = 0, S_BX = S_WIN + SBT * LDS, S_BY = S_BX + SBT * LDS;
 constexpr int S_W = S_BY + SBT * LDS;  // [j][4]: wx re, im, wy re, im
 constexpr int S_U = S_W + 4 * SBT;     // [j][2]
 constexpr int S_FL = S_U + 2 * SBT;    // [j][2] int
-constexpr int N_SMEM = S_FL + 2 * SBT;
+constexpr int S_SIZE = S_FL + 2 * SBT;
+constexpr int S_STAGE = N_OPER;
+constexpr int N_SMEM = S_STAGE + 2 * S_SIZE;
+static_assert(S_STAGE % 4 == 0 && S_SIZE % 4 == 0, "16-byte staging");
 // partial tile (float2) and corner exchange, reusing the operand area at the end
 constexpr int PART = PW * PW + 2 * B2 * PW + B2 * B2;
 constexpr int O_CS = 2 * PART;  // [2 warps][16][8] floats
@@ -428,7 +431,7 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
   const int it = order[blockIdx.x];  // work item (larger items launch first)
   const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
   const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
-  stage(sm, wid, lane, s0, min(SBT, s1 - s0), win, w, bf, u, perm, fl, M);
+  stage(sm + S_STAGE, wid, lane, s0, min(SBT, s1 - s0), win, w, bf, u, perm, fl, M);
   cp_commit();
   for (int i = threadIdx.x; i < N_OPER; i += blockDim.x) sm[i] = 0.0f;
   // accumulators.  Warps 0-1: interior rows m0..m0+15, [re: 0-2 | im: 3-5][n-block].
@@ -447,10 +450,17 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
   // phase-1 role: the 32-wide operand this warp owns and where its last window sat
   float* Own = sm + (wid == 0 ? O_AR : wid == 1 ? O_AI : wid == 2 ? O_BX : O_BY);
   int prev = -1;
-  for (int sb = s0; sb < s1; sb += SBT) {
+  int buf = 0;
+  for (int sb = s0; sb < s1; sb += SBT, buf ^= 1) {
     const int nb = min(SBT, s1 - sb);
     cp_wait_all();
     __syncthreads();  // staging of this batch visible; phase 2 of the last batch done
+    // the next batch's inputs go to the other buffer (last read by the previous phase 1)
+    if (sb + SBT < s1)
+      stage(sm + S_STAGE + (buf ^ 1) * S_SIZE, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, u, perm,
+            fl, M);
+    cp_commit();
+    const float* st = sm + S_STAGE + buf * S_SIZE;
     {
       const int j = lane;
       float* row = Own + j * LDO;
@@ -460,12 +470,12 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         prev = -1;
       }
       if (j < nb) {
-        const float4 ww = *reinterpret_cast<const float4*>(sm + S_W + 4 * j);
+        const float4 ww = *reinterpret_cast<const float4*>(st + S_W + 4 * j);
         const float2 wxs = make_float2(ww.x, ww.y), wys = make_float2(ww.z, ww.w);
-        const float2 us = *reinterpret_cast<const float2*>(sm + S_U + 2 * j);
-        const int* flj = reinterpret_cast<const int*>(sm + S_FL + 2 * j);
+        const float2 us = *reinterpret_cast<const float2*>(st + S_U + 2 * j);
+        const int* flj = reinterpret_cast<const int*>(st + S_FL + 2 * j);
         const int pos = (wid == 3) ? flj[1] - oy + 1 : flj[0] - ox + 1;
-        const float* tp = sm + S_WIN + j * LDS + (wid == 3 ? W : 0);
+        const float* tp = st + S_WIN + j * LDS + (wid == 3 ? W : 0);
         const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
         const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         float scale = 1.0f;
@@ -477,7 +487,7 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         for (int a = 0; a < W; ++a) row[pos + a] = scale * tap[a];
         prev = pos;
         // boundary operands: warp 0 V0 (x-sides), 1 V1 (y-sides), 2 A = u conj(bx), 3 conj(by)
-        const float* bp = sm + ((wid == 0 || wid == 2) ? S_BX : S_BY) + j * LDS;
+        const float* bp = st + ((wid == 0 || wid == 2) ? S_BX : S_BY) + j * LDS;
         const float2 uwx = cmulc(us, wxs);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -514,9 +524,7 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         }
       }
     }
-    __syncthreads();  // operands complete; staging free
-    if (sb + SBT < s1) stage(sm, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, u, perm, fl, M);
-    cp_commit();
+    __syncthreads();  // operands complete
     // The three products of the split go term by term over the warp's tiles, so
     // that consecutive MMAs never update the same accumulator.
     if (wid < 2) {
