@@ -637,8 +637,6 @@ constexpr int SBT = 32, W = 8, B2 = 8, TILE = 16, PW = TILE + W;
 constexpr int LDP = 28;  // rows of the (hi, lo) item operands [n][k] in pairs: conflict-free 64-bit fragments
 constexpr int LDX = 20;  // rows of the corner operands (K = 16), stored [ky][k]
 constexpr int LDS = 20;  // staged rows of 16 floats
-constexpr int LDH = 56;  // H rows: 24 complex + pad (floats)
-constexpr int LDQ = 18;  // Q0, Q1, RR rows: 8 complex + pad (floats)
 // item operands (floats; the paired planes hold float2 (hi, lo) per element)
 constexpr int I_GR = 0, I_GI = I_GR + 2 * PW * LDP;  // [x][y]
 constexpr int I_S0R = I_GI + 2 * PW * LDP, I_S0I = I_S0R + 2 * B2 * LDP;  // [k][y]
@@ -646,15 +644,15 @@ constexpr int I_S1R = I_S0I + 2 * B2 * LDP, I_S1I = I_S1R + 2 * B2 * LDP;  // [k
 constexpr int I_XR = I_S1I + 2 * B2 * LDP;  // [ky][k]: k < 8 Re X[ky][k], k >= 8 -Im X[ky][k - 8]
 constexpr int I_XI = I_XR + B2 * LDX;       // [ky][k]: k < 8 Im X[ky][k], k >= 8  Re X[ky][k - 8]
 constexpr int N_ITEM = I_XI + B2 * LDX;
-// products of the batch
-constexpr int O_H = N_ITEM, O_Q0 = O_H + SBT * LDH, O_Q1 = O_Q0 + SBT * LDQ, O_RR = O_Q1 + SBT * LDQ;
+// the four terms of each sample (interior, x-sides, y-sides, corners), complex [term][sample]
+constexpr int O_T = N_ITEM;
 // staged inputs, two buffers: taps wx | wy, bx, by (complex), phases wx wy, grid indices
 constexpr int ST_WIN = 0, ST_BX = ST_WIN + SBT * LDS, ST_BY = ST_BX + SBT * LDS, ST_W = ST_BY + SBT * LDS;
 constexpr int ST_FL = ST_W + 4 * SBT;
 constexpr int ST_SIZE = ST_FL + 2 * SBT;
-constexpr int S_STAGE = O_RR + SBT * LDQ;
+constexpr int S_STAGE = O_T + 4 * 2 * SBT;
 constexpr int N_SMEM = S_STAGE + 2 * ST_SIZE;
-static_assert(S_STAGE % 4 == 0 && ST_SIZE % 4 == 0 && O_H % 2 == 0, "16-byte staging, 8-byte products");
+static_assert(S_STAGE % 4 == 0 && ST_SIZE % 4 == 0 && O_T % 2 == 0, "16-byte staging, 8-byte terms");
 
 __device__ inline void stage(float* st, int wid, int lane, int sb, int nb, const float* __restrict__ win,
                              const float2* __restrict__ w, const float2* __restrict__ bf,
@@ -755,7 +753,6 @@ static __global__ void __launch_bounds__(128, 4) k_interp2d_tc(
     sm[I_XI + ky * LDX + kx] = X.y;
     sm[I_XI + ky * LDX + B2 + kx] = X.x;
   }
-  const int ps = threadIdx.x >> 2, pq = threadIdx.x & 3;  // combine step: sample, term
   double nacc = 0.0;
   int buf = 0;
   for (int sb = s0; sb < s1; sb += SBT, buf ^= 1) {
@@ -805,13 +802,32 @@ static __global__ void __launch_bounds__(128, 4) k_interp2d_tc(
             for (int ri = 0; ri < 2; ++ri)
               mma(acc[3 * ri + nbk], term == 2 ? al : ah, term == 1 ? bl[ri][nbk] : bh[ri][nbk]);
       }
+      // interior term: the lane holds H[s][x] for its two samples and six columns x;
+      // sum wx_s[x - px_s] H[s][x] over them, then over the quad's four lanes
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = m0 + g + ((q & 2) ? 8 : 0);
+      for (int h = 0; h < 2; ++h) {
+        const int s = m0 + g + 8 * h;
+        const int px = (s < nb) ? sfl[2 * s] - ox : -2 * W;
+        float2 v = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int nbk = 0; nbk < 3; ++nbk) {
-          const int c = 8 * nbk + 2 * t + (q & 1);
-          *reinterpret_cast<float2*>(sm + O_H + r * LDH + 2 * c) = make_float2(acc[nbk][q], acc[3 + nbk][q]);
+        for (int nbk = 0; nbk < 3; ++nbk)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int a = 8 * nbk + 2 * t + e - px;
+            if ((unsigned)a < (unsigned)W) {
+              const float tap = st[ST_WIN + s * LDS + a];
+              v.x += tap * acc[nbk][2 * h + e];
+              v.y += tap * acc[3 + nbk][2 * h + e];
+            }
+          }
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+        if (t == 0 && s < nb) {
+          const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * s);
+          *reinterpret_cast<float2*>(sm + O_T + 2 * s) =
+              cmul(cmul(make_float2(ww.x, ww.y), make_float2(ww.z, ww.w)), v);
         }
       }
     } else {
@@ -866,70 +882,49 @@ static __global__ void __launch_bounds__(128, 4) k_interp2d_tc(
 #pragma unroll
           for (int ri = 0; ri < 2; ++ri) mma(acc[4 + ri], term == 2 ? al : ah, term == 1 ? bl[ri] : bh[ri]);
       }
-      float* Q = sm + (xs ? O_Q0 : O_Q1);
+      // side and corner terms: the lane holds Q[s][k] and RR[s][k] for k = 2t, 2t + 1;
+      // sum the boundary factors times them, then over the quad's four lanes
+      const float* bq = st + (xs ? ST_BX : ST_BY);  // x-sides pair with bx, y-sides with by
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = g + ((q & 2) ? 8 : 0), c = 2 * t + (q & 1);
+      for (int h = 0; h < 6; ++h) {  // rows: side block 0 (g, g+8), block 1 (16+g, 24+g), corners (rc+g, rc+g+8)
+        const int s = (h < 4) ? g + 8 * (h & 1) + 16 * (h >> 1) : rc + g + 8 * (h & 1);
+        const int tr = (h < 4) ? 2 * (h >> 1) : 4;  // tile pair of this row
+        const float* fac = (h < 4) ? bq : st + ST_BY;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (s < nb) {
 #pragma unroll
-        for (int mb = 0; mb < 2; ++mb)
-          *reinterpret_cast<float2*>(Q + (16 * mb + r) * LDQ + 2 * c) = make_float2(acc[2 * mb][q], acc[2 * mb + 1][q]);
-        *reinterpret_cast<float2*>(sm + O_RR + (rc + r) * LDQ + 2 * c) = make_float2(acc[4][q], acc[5][q]);
-      }
-    }
-    __syncthreads();  // products complete
-    {
-      float2 c = make_float2(0.0f, 0.0f);
-      const int j = ps;
-      if (j < nb) {
-        const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * j);
-        const float2 wxs = make_float2(ww.x, ww.y), wys = make_float2(ww.z, ww.w);
-        if (pq == 0) {  // interior
-          const int px = sfl[2 * j] - ox;
-          const float* tp = st + ST_WIN + j * LDS;
-          const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
-          const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-          const float2* hr = reinterpret_cast<const float2*>(sm + O_H + j * LDH) + px;
-          float2 vi = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int a = 0; a < W; ++a) {
-            const float2 hv = hr[a];
-            vi.x += tap[a] * hv.x;
-            vi.y += tap[a] * hv.y;
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * t + e;
+            const float2 f = *reinterpret_cast<const float2*>(fac + s * LDS + 2 * k);
+            v = cadd(v, cmul(f, make_float2(acc[tr][2 * (h & 1) + e], acc[tr + 1][2 * (h & 1) + e])));
           }
-          c = cmul(cmul(wxs, wys), vi);
-        } else {  // 1: x-sides with bx, 2: y-sides with by, 3: corners with by
-          const float* bp = st + (pq == 1 ? ST_BX : ST_BY) + j * LDS;
-          const float2* qr = reinterpret_cast<const float2*>(sm + (pq == 1 ? O_Q0 : pq == 2 ? O_Q1 : O_RR) + j * LDQ);
-          float2 sacc = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int h = 0; h < 4; ++h) {
-            const float4 f = *reinterpret_cast<const float4*>(bp + 4 * h);
-            sacc = cadd(sacc, cmul(make_float2(f.x, f.y), qr[2 * h]));
-            sacc = cadd(sacc, cmul(make_float2(f.z, f.w), qr[2 * h + 1]));
+        }
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+        if (t == 0 && s < nb) {
+          if (h < 4) {  // x-sides times wy, y-sides times wx
+            const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * s);
+            v = xs ? cmul(make_float2(ww.z, ww.w), v) : cmul(make_float2(ww.x, ww.y), v);
           }
-          c = (pq == 1) ? cmul(wys, sacc) : (pq == 2) ? cmul(wxs, sacc) : sacc;
+          *reinterpret_cast<float2*>(sm + O_T + 2 * ((h < 4 ? (xs ? 1 : 2) : 3) * SBT + s)) = v;
         }
       }
-      // (c0 + c1) + (c2 + c3) in every lane of the sample's group
-      c.x += __shfl_xor_sync(0xffffffffu, c.x, 1);
-      c.y += __shfl_xor_sync(0xffffffffu, c.y, 1);
-      c.x += __shfl_xor_sync(0xffffffffu, c.x, 2);
-      c.y += __shfl_xor_sync(0xffffffffu, c.y, 2);
-      if (pq == 0 && j < nb) {
-        const int s = sb + j;
-        y[perm ? perm[s] : s] = c;
-        nacc += (double)c.x * c.x + (double)c.y * c.y;
-      }
+    }
+    __syncthreads();  // terms complete
+    if (wid == 0 && lane < nb) {  // y = (interior + x-sides) + (y-sides + corners)
+      const float2* tm = reinterpret_cast<const float2*>(sm + O_T);
+      const float2 c = cadd(cadd(tm[lane], tm[SBT + lane]), cadd(tm[2 * SBT + lane], tm[3 * SBT + lane]));
+      const int s = sb + lane;
+      y[perm ? perm[s] : s] = c;
+      nacc += (double)c.x * c.x + (double)c.y * c.y;
     }
   }
-  if (norm_part) {  // ||y||^2 over this item's samples: lanes, then warps, in a fixed order
+  if (norm_part) {  // ||y||^2 over this item's samples (all in warp 0): lanes in a fixed order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
-    __syncthreads();  // the products are no longer read
-    double* wsum = reinterpret_cast<double*>(sm + O_H);
-    if (lane == 0) wsum[wid] = nacc;
-    __syncthreads();
-    if (threadIdx.x == 0) norm_part[it] = ((wsum[0] + wsum[1]) + wsum[2]) + wsum[3];
+    if (threadIdx.x == 0) norm_part[it] = nacc;
   }
 }
 
