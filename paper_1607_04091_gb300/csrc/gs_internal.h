@@ -172,22 +172,42 @@ gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStrea
 // order (y[perm[s]]); perm == NULL: samples in the plan's sorted order.
 // norm_part != NULL (2D plans only): the interpolation also writes, per work
 // item i, the sum of |y_s|^2 over its samples to norm_part[i] (nwork values).
+template <typename R> struct PUpdate;
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part = nullptr);
+                 double* norm_part = nullptr, const PUpdate<R>* pu = nullptr);
+// Solver scalars (float64 slots of Plan::scal) and stop flags (Plan::flag[0]);
+// Plan::flag[FL_ARRIVE] counts the CTAs of a fused CG step that have finished.
+enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
+enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
+constexpr int FL_ARRIVE = 4;
+
 // The vector update of a CG step fused into the adjoint's last pass (2D plans):
 // after z = T^H q, x += alpha p and s -= alpha z over all coefficients, with the
 // per-CTA partial sums of the new ||s||^2 in part (one per coefficient row, N
 // values); skipped while flag[0] != 0.  join_branch >= 0: side branch to join
 // before that pass (where alpha is computed).
+// With scal != NULL the last CTA to finish also closes the step: it sums the
+// partials in row order into gamma' = ||s||^2 and sets beta = gamma'/gamma, the
+// iteration count and the stop flag (what k_beta_p does otherwise); the p update
+// p = s + beta p then happens in the next forward pass (PUpdate).
 template <typename R> struct CgStep {
   C<R>* x;
   const C<R>* p;
   C<R>* s;
   const double* alpha;
-  const int* flag;
+  int* flag;
   double* part;
   int join_branch;
+  double* scal;
+};
+// p = s + beta p fused into the first forward pass of the next CG step (2D plans);
+// skipped while flag[0] != F_RUN.
+template <typename R> struct PUpdate {
+  C<R>* p;
+  const C<R>* s;
+  const double* beta;
+  const int* flag;
 };
 template <typename R>
 gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,

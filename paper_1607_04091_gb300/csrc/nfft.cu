@@ -435,11 +435,16 @@ __global__ void k_adj1d_fft(const C<R>* __restrict__ grid, const R* __restrict__
 // pass 1: x-transform of every coefficient row j -> hbuf[j][:]
 template <typename R>
 __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ deap, int N, int n,
-                              int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf) {
+                              int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf,
+                              PUpdate<R> pu) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
+  // fused CG direction update of these rows: p = s + beta p (x is p), every
+  // coefficient of the row visited once below
+  const bool upd = pu.p != nullptr && pu.flag[0] == F_RUN;
+  const R bt = upd ? (R)pu.beta[0] : (R)0;
   // grid point l of row r holds coefficient i = l + N/2 (mod n), deapodised, or 0
   batched<PPT_ROW, C<R>>(
       nr * n,
@@ -448,8 +453,14 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
         const int i = (l + N / 2) & (n - 1);
         C<R> v = mk<R>(0, 0);
         if (i < N) {
+          const int64_t k = (int64_t)(j0 + r) * N + i;
           const R dv = deap[i];
-          const C<R> xv = x[(int64_t)(j0 + r) * N + i];
+          C<R> xv = upd ? pu.p[k] : x[k];  // x is p when updating (read through the writable pointer)
+          if (upd) {
+            const C<R> sv = pu.s[k];
+            xv = mk<R>(sv.x + bt * xv.x, sv.y + bt * xv.y);
+            pu.p[k] = xv;
+          }
           if (dv != (R)0) v = cscale(xv, dv);
         }
         return v;
@@ -615,9 +626,26 @@ __global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const in
     const int q0 = (g - cn[ci] * tile + m) & (n - 1);
     const int r0 = (which == 0) ? work_start[cn[ci] * nbx] : wcol_start[cn[ci]];
     const int r1 = (which == 0) ? work_start[(cn[ci] + 1) * nbx] : wcol_start[cn[ci] + 1];
-    for (int r = r0 + wl; r < r1; r += nl) {
-      const int wi = (which == 0) ? r : wcol[r];
-      for (int q = q0; q < PW; q += n) acc = cadd(acc, part[wi * stride + off + q]);
+    if (q0 >= PW) continue;  // this bin's segments do not reach g
+    // items r0 + wl, + nl, ...: loads issued four at a time, summed in item order
+    for (int r = r0 + wl; r < r1; r += 4 * nl) {
+      C<R> v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int rr = r + u * nl;
+        v[u] = mk<R>(0, 0);
+        if (rr < r1) {
+          const int wi = (which == 0) ? rr : wcol[rr];
+          v[u] = part[wi * stride + off + q0];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = cadd(acc, v[u]);
+      for (int u = 0; u < 4; ++u)  // further periods (grids shorter than a padded tile)
+        for (int q = q0 + n; q < PW; q += n) {
+          const int rr = r + u * nl;
+          if (rr < r1) acc = cadd(acc, part[((which == 0) ? rr : wcol[rr]) * stride + off + q]);
+        }
     }
   }
   red[threadIdx.x] = acc;
@@ -729,10 +757,40 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
     __syncthreads();
+    __shared__ int last;
     if (threadIdx.x == 0) {
       double tsum = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[w];
       cg.part[blockIdx.x] = tsum;
+      last = 0;
+      if (cg.scal) {  // publish the partial, then count this CTA in
+        __threadfence();
+        last = (atomicAdd(cg.flag + FL_ARRIVE, 1) == (int)gridDim.x - 1);
+      }
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last CTA: gamma' = sum of the partials in row order, beta, stop test
+    __threadfence();
+    double g = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) g += __ldcg(cg.part + i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = g;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double gs = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gs += wsum[w];
+      double* sc = cg.scal;
+      const double beta = gs / sc[S_GAMMA];
+      sc[S_BETA] = beta;
+      sc[S_GNEW] = gs;
+      sc[S_ITER] += 1.0;
+      if (!isfinite(beta)) cg.flag[0] = F_BREAK;
+      else if (gs <= sc[S_THR2]) cg.flag[0] = F_CONV;
+      else if (sc[S_ITER] >= sc[S_MAXIT]) cg.flag[0] = F_MAXIT;
+      cg.flag[FL_ARRIVE] = 0;
     }
   }
 }
@@ -764,7 +822,7 @@ constexpr int FOUR_STEP_N = 4096;  // 1D grids from this size use the two-pass F
 // ---------------------------------------------------------------- host drivers
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part) {
+                 double* norm_part, const PUpdate<R>* pu) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b;
   const int64_t M = P->M;
   const R beta = (R)D.beta;
@@ -792,7 +850,8 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
               k_fwd2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw,
-                                                                        D.hbuf));
+                                                                        D.hbuf,
+                                                                        pu ? *pu : PUpdate<R>{nullptr, nullptr, nullptr, nullptr}));
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
@@ -889,7 +948,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
-    const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1};
+    const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
               k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
@@ -972,7 +1031,7 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z, CgStep<R>{nullptr, nullptr, nullptr,
                                                                                             nullptr, nullptr, nullptr,
-                                                                                            -1}));
+                                                                                            -1, nullptr}));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -992,9 +1051,9 @@ gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t
 }
 
 template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
-                                 double*);
+                                 double*, const PUpdate<float>*);
 template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t,
-                                  double*);
+                                  double*, const PUpdate<double>*);
 template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
                                   const CgStep<float>*);
 template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,

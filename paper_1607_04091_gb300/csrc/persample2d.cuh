@@ -488,7 +488,7 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         prev = pos;
         // boundary operands: warp 0 V0 (x-sides), 1 V1 (y-sides), 2 A = u conj(bx), 3 conj(by)
         const float* bp = st + ((wid == 0 || wid == 2) ? S_BX : S_BY) + j * LDS;
-        const float2 uwx = cmulc(us, wxs);
+        const float2 uwx = cmulc(us, wxs), uwy = cmulc(us, wys);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const float4 f = *reinterpret_cast<const float4*>(bp + 4 * h);
@@ -497,7 +497,7 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
           for (int e = 0; e < 2; ++e) {
             const int k = 2 * h + e;
             if (wid == 0) {
-              const float2 v0 = cmulc(cmulc(us, bk[e]), wys);
+              const float2 v0 = cmulc(uwy, bk[e]);
               sm[O_V0R + k * LDT + j] = v0.x;
               sm[O_V0I + k * LDT + j] = v0.y;
             } else if (wid == 1) {
@@ -712,7 +712,7 @@ __device__ inline void put_pair(float* B, int r, int c, float v) {
 }
 }  // namespace tci
 
-static __global__ void __launch_bounds__(128, 4) k_interp2d_tc(
+static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
     const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl,
     const float* __restrict__ win, const float2* __restrict__ w, const float2* __restrict__ bf,
     const float2* __restrict__ grid, const float2* __restrict__ hbuf, const float2* __restrict__ side, int n,

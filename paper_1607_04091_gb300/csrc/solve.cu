@@ -23,11 +23,9 @@ namespace gs {
 namespace {
 
 constexpr int RED_BLOCKS = 512;
-enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
 // scalars of the device-side mixed solve (solve graph)
 enum { G_TOL2 = 20, G_MAXIT, G_MAXOUT, G_IRTOL2, G_HB2, G_HY2, G_THR2, G_NS2, G_OUTER, G_TOTAL, G_NR2, G_STOP,
        G_WARM };
-enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
 
 template <typename T> __device__ inline double sqn(T v) { return (double)v.x * v.x + (double)v.y * v.y; }
 
@@ -190,6 +188,8 @@ __global__ void k_to32(float2* __restrict__ o, const double2* __restrict__ in, i
 __global__ void k_init_pass(double* scal, int* flag, double thr2, double maxit) {
   scal[S_GAMMA] = scal[S_TMP];
   scal[S_GNEW] = scal[S_TMP];
+  scal[S_BETA] = 0.0;  // the first fused p update leaves p = s
+  flag[FL_ARRIVE] = 0;
   scal[S_S0] = scal[S_TMP];
   scal[S_THR2] = thr2;
   scal[S_ITER] = 0.0;
@@ -234,9 +234,13 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
   // q = T p with ||q||^2 partials: per work item from the 2D interpolation, else a grid reduction
   int np = RED_BLOCKS;
   gs_status s;
+  // 2D CGNR: the step is closed by the adjoint's last pass and p = s + beta p is
+  // applied by the next forward pass (no separate beta / p kernel)
+  const bool fused = normal_eq && !P->direct && P->dims == 2;
   if (!P->direct && P->dims == 2) {
     np = P->nwork;
-    s = nfft_T<R>(P, D, D.vp, D.vq, nullptr, st, P->red);
+    const PUpdate<R> pu{D.vp, D.vs, P->scal + S_BETA, P->flag};
+    s = nfft_T<R>(P, D, D.vp, D.vq, nullptr, st, P->red, fused ? &pu : nullptr);
     if (s != GS_OK) return s;
   } else {
     s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
@@ -255,7 +259,7 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
     GS_CUDA(cudaGetLastError());
     if (!P->direct && P->dims == 2) {
       // 2D: the x and s update runs in the adjoint's last pass, one partial per coefficient row
-      const CgStep<R> cg{D.vx, D.vp, D.vs, P->scal + S_ALPHA, P->flag, red_s, 2};
+      const CgStep<R> cg{D.vx, D.vp, D.vs, P->scal + S_ALPHA, P->flag, red_s, 2, P->scal};
       GS_TRY(nfft_TH<R>(P, D, D.vq, D.vz, nullptr, st, &cg));
       np_s = (int)P->N;
     } else {
@@ -273,7 +277,8 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
     if (s != GS_OK) return s;
     GS_LAUNCH("cgls_norm2", st, k_norm2<R><<<gs, 256, 0, st>>>(D.vs, nc, red_s, P->flag));
   }
-  GS_LAUNCH("cgls_scalar", st, k_beta_p<R><<<gs, 256, 0, st>>>(red_s, np_s, D.vp, D.vs, nc, P->scal, P->flag));
+  if (!fused)
+    GS_LAUNCH("cgls_scalar", st, k_beta_p<R><<<gs, 256, 0, st>>>(red_s, np_s, D.vp, D.vs, nc, P->scal, P->flag));
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }
@@ -472,6 +477,8 @@ __global__ void k_pass_init(double* scal, int* flag) {
   const double thr = fmax(0.25 * scal[G_THR2], scal[G_IRTOL2] * ns2);
   scal[S_GAMMA] = ns2;
   scal[S_GNEW] = ns2;
+  scal[S_BETA] = 0.0;  // the first fused p update leaves p = s
+  flag[FL_ARRIVE] = 0;
   scal[S_S0] = ns2;
   scal[S_THR2] = thr;
   scal[S_ITER] = 0.0;
