@@ -644,13 +644,15 @@ constexpr int I_S1R = I_S0I + 2 * B2 * LDP, I_S1I = I_S1R + 2 * B2 * LDP;  // [k
 constexpr int I_XR = I_S1I + 2 * B2 * LDP;  // [ky][k]: k < 8 Re X[ky][k], k >= 8 -Im X[ky][k - 8]
 constexpr int I_XI = I_XR + B2 * LDX;       // [ky][k]: k < 8 Im X[ky][k], k >= 8  Re X[ky][k - 8]
 constexpr int N_ITEM = I_XI + B2 * LDX;
-// the four terms of each sample (interior, x-sides, y-sides, corners), complex [term][sample]
+// the four terms of each sample (interior, x-sides, y-sides, corners), complex
+// [buffer][term][sample]: batch b's terms are summed during batch b + 1
 constexpr int O_T = N_ITEM;
+constexpr int T_SIZE = 4 * 2 * SBT;
 // staged inputs, two buffers: taps wx | wy, bx, by (complex), phases wx wy, grid indices
 constexpr int ST_WIN = 0, ST_BX = ST_WIN + SBT * LDS, ST_BY = ST_BX + SBT * LDS, ST_W = ST_BY + SBT * LDS;
 constexpr int ST_FL = ST_W + 4 * SBT;
 constexpr int ST_SIZE = ST_FL + 2 * SBT;
-constexpr int S_STAGE = O_T + 4 * 2 * SBT;
+constexpr int S_STAGE = O_T + 2 * T_SIZE;
 constexpr int N_SMEM = S_STAGE + 2 * ST_SIZE;
 static_assert(S_STAGE % 4 == 0 && ST_SIZE % 4 == 0 && O_T % 2 == 0, "16-byte staging, 8-byte terms");
 
@@ -754,14 +756,28 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
     sm[I_XI + ky * LDX + B2 + kx] = X.x;
   }
   double nacc = 0.0;
-  int buf = 0;
+  // y = (interior + x-sides) + (y-sides + corners) for the samples of a finished batch
+  auto finish = [&](const float* tb, int sbp, int nbp) {
+    if (wid == 0 && lane < nbp) {
+      const float2* tm = reinterpret_cast<const float2*>(tb);
+      const float2 c = cadd(cadd(tm[lane], tm[SBT + lane]), cadd(tm[2 * SBT + lane], tm[3 * SBT + lane]));
+      const int s = sbp + lane;
+      y[perm ? perm[s] : s] = c;
+      nacc += (double)c.x * c.x + (double)c.y * c.y;
+    }
+  };
+  int buf = 0, sb_prev = 0, nb_prev = 0;
   for (int sb = s0; sb < s1; sb += SBT, buf ^= 1) {
     const int nb = min(SBT, s1 - sb);
     cp_wait_all();
-    __syncthreads();  // this batch staged, item operands written; the last combine step done
+    __syncthreads();  // this batch staged, item operands written; the last batch's terms written
     if (sb + SBT < s1)
       stage(sm + S_STAGE + (buf ^ 1) * ST_SIZE, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, fl, M);
     cp_commit();
+    if (sb > s0) finish(sm + O_T + (buf ^ 1) * T_SIZE, sb_prev, nb_prev);
+    sb_prev = sb;
+    nb_prev = nb;
+    float* tbuf = sm + O_T + buf * T_SIZE;
     const float* st = sm + S_STAGE + buf * ST_SIZE;
     const int* sfl = reinterpret_cast<const int*>(st + ST_FL);
     float acc[6][4];
@@ -826,8 +842,7 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
         v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
         if (t == 0 && s < nb) {
           const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * s);
-          *reinterpret_cast<float2*>(sm + O_T + 2 * s) =
-              cmul(cmul(make_float2(ww.x, ww.y), make_float2(ww.z, ww.w)), v);
+          *reinterpret_cast<float2*>(tbuf + 2 * s) = cmul(cmul(make_float2(ww.x, ww.y), make_float2(ww.z, ww.w)), v);
         }
       }
     } else {
@@ -908,19 +923,13 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
             const float4 ww = *reinterpret_cast<const float4*>(st + ST_W + 4 * s);
             v = xs ? cmul(make_float2(ww.z, ww.w), v) : cmul(make_float2(ww.x, ww.y), v);
           }
-          *reinterpret_cast<float2*>(sm + O_T + 2 * ((h < 4 ? (xs ? 1 : 2) : 3) * SBT + s)) = v;
+          *reinterpret_cast<float2*>(tbuf + 2 * ((h < 4 ? (xs ? 1 : 2) : 3) * SBT + s)) = v;
         }
       }
     }
-    __syncthreads();  // terms complete
-    if (wid == 0 && lane < nb) {  // y = (interior + x-sides) + (y-sides + corners)
-      const float2* tm = reinterpret_cast<const float2*>(sm + O_T);
-      const float2 c = cadd(cadd(tm[lane], tm[SBT + lane]), cadd(tm[2 * SBT + lane], tm[3 * SBT + lane]));
-      const int s = sb + lane;
-      y[perm ? perm[s] : s] = c;
-      nacc += (double)c.x * c.x + (double)c.y * c.y;
-    }
   }
+  __syncthreads();  // the last batch's terms written
+  finish(sm + O_T + (buf ^ 1) * T_SIZE, sb_prev, nb_prev);
   if (norm_part) {  // ||y||^2 over this item's samples (all in warp 0): lanes in a fixed order
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
