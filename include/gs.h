@@ -64,7 +64,7 @@ typedef struct {
   int kb_m_lo;  /* Kaiser-Bessel half-width m in 2..8 for GS_FP32 applies [4] */
   int sigma;    /* oversampling factor of the NFFT grid, 2 or 4 [2] */
   int direct;   /* 1: evaluate T entry by entry (O(M N^d) per apply, small problems);
-                   0: NFFT path; -1: choose (direct when M * N^d <= 2^20) [-1] */
+                   0: NFFT path; -1: choose (direct when M * N^d <= 2^16) [-1] */
 } gs_opts;
 
 /* Build a 1D plan: the representation of T (paper: Freq2Wave(xi, "dbp", J[, bandwidth]),
@@ -130,8 +130,9 @@ typedef struct {
                      ||T^H y|| (else the solve starts from x = 0); 0: start from x = 0 [0] */
   int max_outer;  /* refinement passes in GS_SOLVE_MIXED [8] */
   double inner_rtol; /* GS_SOLVE_MIXED: a pass stops when its ||T^H (r - T d)|| falls
-                        by this factor (or below tol ||T^H y|| / 2); 0 = default
-                        [min(1e-4, 0.3 tol) for tol >= 1e-6, else 1e-4] */
+                        by this factor (or below tol ||T^H y|| / 2); the first pass of a
+                        kept starting guess ends at the first inner_rtol^k ||T^H y|| below
+                        its start; 0 = default [1e-3] */
 } gs_solve_opts;
 
 typedef struct {

@@ -187,7 +187,9 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
     }
     P->direct = 0;
   } else {
-    P->direct = (!nfft_ok || (double)M * (double)P->ncoef <= 1048576.0) ? 1 : 0;
+    // direct evaluation (one thread per sample or coefficient, a sincos per entry)
+    // only for tiny problems; the NFFT path is faster from ~2^16 entries
+    P->direct = (!nfft_ok || (double)M * (double)P->ncoef <= 65536.0) ? 1 : 0;
   }
   if (!build_constants(p, &P->k)) {
     set_error("boundary construction failed for p = %d", p);
@@ -284,10 +286,10 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
   }
   gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
   if (opts) o = *opts;
-  // default: for tol >= 1e-6 the first float32 pass aims at tol / 2 directly (one pass
-  // usually meets tol; the float64 check starts another when it does not), for tighter
-  // tolerances each pass gains four orders (float32 passes stagnate near 1e-7)
-  if (o.inner_rtol == 0.0) o.inner_rtol = (o.tol >= 1e-6) ? std::min(1e-4, 0.3 * o.tol) : 1e-4;
+  // default: each float32 pass gains three orders before the float64 residual is
+  // re-formed; the restart keeps float32 drift out of long passes (ill-conditioned
+  // problems) and costs few iterations on well-conditioned ones
+  if (o.inner_rtol == 0.0) o.inner_rtol = 1e-3;
   if (!(o.tol > 0.0) || o.maxit < 1 || (o.mode != GS_SOLVE_FP64 && o.mode != GS_SOLVE_MIXED) || o.max_outer < 1 ||
       !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0)) {
     set_error("bad solve options (tol > 0, maxit >= 1, mode 0/1, max_outer >= 1, 0 < inner_rtol < 1)");
@@ -379,10 +381,10 @@ gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void
   }
   gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
   if (opts) o = *opts;
-  // default: for tol >= 1e-6 the first float32 pass aims at tol / 2 directly (one pass
-  // usually meets tol; the float64 check starts another when it does not), for tighter
-  // tolerances each pass gains four orders (float32 passes stagnate near 1e-7)
-  if (o.inner_rtol == 0.0) o.inner_rtol = (o.tol >= 1e-6) ? std::min(1e-4, 0.3 * o.tol) : 1e-4;
+  // default: each float32 pass gains three orders before the float64 residual is
+  // re-formed; the restart keeps float32 drift out of long passes (ill-conditioned
+  // problems) and costs few iterations on well-conditioned ones
+  if (o.inner_rtol == 0.0) o.inner_rtol = 1e-3;
   if (!(o.tol > 0.0) || o.maxit < 1 || (o.mode != GS_SOLVE_FP64 && o.mode != GS_SOLVE_MIXED) || o.max_outer < 1 ||
       !(o.inner_rtol > 0.0 && o.inner_rtol < 1.0)) {
     set_error("bad solve options (tol > 0, maxit >= 1, mode 0/1, max_outer >= 1, 0 < inner_rtol < 1)");

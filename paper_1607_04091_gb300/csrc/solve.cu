@@ -472,9 +472,27 @@ __global__ void k_outer_enter(cudaGraphConditionalHandle h, const double* scal) 
                   scal[G_TOTAL] < scal[G_MAXIT];
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
+// Squared stop threshold of a refinement pass that starts at ||T^H r||^2 = ns2:
+// a pass gains irtol (relative to its own start; a restart from the float64
+// residual then removes the float32 drift), and never aims below tol / 2.  The
+// first pass of a warm start instead ends at the first level irtol^k ||T^H y||
+// below its start, the point where a zero start's pass ends, so that it joins
+// that schedule rather than shifting it.
+__host__ __device__ inline double pass_threshold(double ns2, double hb2, double tol2, double irtol2,
+                                                 bool first_warm) {
+  double t2 = irtol2 * ns2;
+  if (first_warm) {
+    double lev2 = irtol2;
+    for (int k = 0; k < 64 && lev2 * hb2 >= ns2; ++k) lev2 *= irtol2;
+    t2 = lev2 * hb2;
+  }
+  return fmax(0.25 * tol2 * hb2, t2);
+}
+
 __global__ void k_pass_init(double* scal, int* flag) {
   const double ns2 = scal[S_TMP];
-  const double thr = fmax(0.25 * scal[G_THR2], scal[G_IRTOL2] * ns2);
+  const double thr = pass_threshold(ns2, scal[G_HB2], scal[G_TOL2], scal[G_IRTOL2],
+                                    scal[G_OUTER] == 0.0 && scal[G_WARM] != 0.0);
   scal[S_GAMMA] = ns2;
   scal[S_GNEW] = ns2;
   scal[S_BETA] = 0.0;  // the first fused p update leaves p = s
@@ -772,15 +790,17 @@ gs_status solve(Plan* P, const double* y_user, double* x_user, const gs_solve_op
       return err;
     };
     if (o.x0_given || hi) GS_TRY(check_value());
+    bool warm = o.x0_given;
     if (o.x0_given && ns2 >= hb2) {  // warm start not better than zero: zero start
       GS_CUDA(cudaMemsetAsync(x64, 0, nc * sizeof(double2), st));
       GS_LAUNCH("solve_copy", st, k_copy<double><<<grid_for(M), 256, 0, st>>>((double2*)P->r64, y64, M));
       GS_TRY(check_value());
       GS_LAUNCH("solve_set_scal", st, k_set_scal<<<1, 1, 0, st>>>(P->scal, G_WARM, 0.0));
+      warm = false;
     }
     for (int outer = 0; outer < o.max_outer; ++outer) {
       if (ns2 <= thr2 || total >= o.maxit) break;
-      double thr_pass = std::max(0.25 * thr2, o.inner_rtol * o.inner_rtol * ns2);
+      double thr_pass = pass_threshold(ns2, hb2, o.tol * o.tol, o.inner_rtol * o.inner_rtol, outer == 0 && warm);
       int it = 0;
       GS_TRY(cgls_pass<float>(P, P->f, thr_pass, o.maxit - total, check, true, st, &it, &stop));
       total += it;
