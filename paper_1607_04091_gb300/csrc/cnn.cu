@@ -553,11 +553,6 @@ __global__ void k_c128_to_c64(const double2* __restrict__ a, float2* __restrict_
     b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
-__global__ void k_res_c128(const double2* __restrict__ y, const double2* __restrict__ q, float2* __restrict__ r,
-                           int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r[i] = make_float2((float)(y[i].x - q[i].x), (float)(y[i].y - q[i].y));
-}
 
 }  // namespace
 }  // namespace gs

@@ -870,7 +870,6 @@ template <typename R>
 gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,
                   const CgStep<R>* cg) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
-  const int64_t M = P->M;
   const R beta = (R)D.beta;
   const int m = D.m, tile = P->tile;
   if (P->nwork == 0) {
@@ -964,7 +963,6 @@ template <typename R>
 gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
                           cudaStream_t st) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
-  const int64_t M = P->M;
   const R beta = (R)D.beta;
   const int m = D.m, tile = P->tile;
   if (P->nwork == 0) {

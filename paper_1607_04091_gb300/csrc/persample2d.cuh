@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int m = W / 2;
   const int b2 = (B2 >= 0) ? B2 : 2 * b_rt;
+  const int b2m = b2 > 0 ? b2 : 1;  // divisor for corner indices (no corners when b2 = 0)
   const int b = b2 / 2;
   const int PW = tile + W;  // staged row i <-> grid point o - m + 1 + i
   const int nm = n - 1;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4 ? 8 : 2)) k_interp2d(
     S1[i] = hbuf[(int64_t)bcol(k, b, N) * n + ((gx0 + c) & nm)];
   }
   for (int t = threadIdx.x; t < b2 * b2; t += blockDim.x) {
-    const int kx = t % b2, ky = t / b2;
+    const int kx = t % b2m, ky = t / b2m;
     XC[t] = x[(int64_t)bcol(ky, b, N) * N + bcol(kx, b, N)];
   }
   __syncthreads();
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(256) k_spread2d(
     C<R>* __restrict__ part, int64_t stride) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int b2 = (B2 >= 0) ? B2 : 2 * b_rt;
+  const int b2m = b2 > 0 ? b2 : 1;  // divisor for corner indices (no corners when b2 = 0)
   const int PW = tile + W;
   const int wsz = PW * PW + 2 * b2 * PW;
   const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -190,8 +192,8 @@ __global__ void __launch_bounds__(256) k_spread2d(
   for (int q = 0; q < NCQ; ++q) {
     const int ch = lane + 32 * q;
     cc[q] = mk<R>(0, 0);
-    cka[q] = (ch < b2 * b2) ? 3 + ch % b2 : 0;       // A[kx]
-    ckb[q] = (ch < b2 * b2) ? 3 + b2 + ch / b2 : 0;  // conj(by[ky])
+    cka[q] = (ch < b2 * b2) ? 3 + ch % b2m : 0;       // A[kx]
+    ckb[q] = (ch < b2 * b2) ? 3 + b2 + ch / b2m : 0;  // conj(by[ky])
   }
   const int it = order[blockIdx.x];  // work item (larger items launch first)
   const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];

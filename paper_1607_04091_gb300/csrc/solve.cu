@@ -555,7 +555,6 @@ gs_status add_while(cudaGraph_t parent, cudaGraphNode_t* dep, cudaGraphCondition
   return GS_OK;
 }
 
-__global__ void k_set_ns2(double* scal) { scal[G_NS2] = scal[S_TMP]; }
 __global__ void k_set_scal(double* scal, int slot, double v) { scal[slot] = v; }
 
 // warm start worse than zero (||T^H r0|| >= ||T^H y||): restart from x = 0, r = y,
