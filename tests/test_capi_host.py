@@ -77,3 +77,25 @@ def test_host_constants_match_oracle(p):
         assert np.max(np.abs(c["U_" + side] - e.U)) < tol
         assert np.max(np.abs(c["V_" + side] - e.V)) < tol
         assert np.max(np.abs(c["v0_" + side] - e.v1_0)) < 10 * tol
+
+
+def test_plan_rejects_empty_sample_sets():
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(np.zeros(0), 2, 5, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_2d(np.zeros((0, 2)), 2, 5, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+
+
+def test_nfft_path_beyond_the_grid_limits_is_unsupported():
+    """1D grids n = 2 * 2^J above 2^20 and 2D grids above 1024 have no NFFT path;
+    asking for it explicitly is GS_EUNSUPPORTED (the automatic choice falls back to
+    direct evaluation)."""
+    xi = np.linspace(-10, 10, 50)
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(xi, 2, 20, stream=_NoStream(), direct=0)
+    assert e.value.status == gs.GS_EUNSUPPORTED
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_2d(np.zeros((10, 2)), 2, 10, stream=_NoStream(), direct=0)
+    assert e.value.status == gs.GS_EUNSUPPORTED
