@@ -165,6 +165,10 @@ inline int fft_threads(int nb, int n) {
   return t < 64 ? 64 : (t > 1024 ? 1024 : t);
 }
 
+// the adjoint's last pass also updates a coefficient row per CTA in the CG solver:
+// at least 128 threads
+inline int adj1_threads(int nb, int n) { return std::max(128, fft_threads(nb, n)); }
+
 // for t = threadIdx.x, + blockDim.x, ... < total: v = load(t), then store(t, v), in
 // groups of LB per thread whose loads are all issued before the group's stores
 // (the pass kernels have few warps, so memory latency is hidden by batching)
@@ -949,7 +953,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
     const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
-              k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, adj1_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z, cgv));
   }
@@ -1025,7 +1029,7 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
-              k_adj2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
+              k_adj2d_pass1<R><<<(N + rows - 1) / rows, adj1_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z, CgStep<R>{nullptr, nullptr, nullptr,
                                                                                             nullptr, nullptr, nullptr,

@@ -827,17 +827,20 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
         const int s = m0 + g + 8 * h;
         const int px = (s < nb) ? sfl[2 * s] - ox : -2 * W;
         float2 v = make_float2(0.0f, 0.0f);
+        // the lane's columns 8 nbk + 2t + e (nbk = 0..2) are 8 apart, so at most one
+        // of them falls in the window [px, px + 8): block nb_e, tap a_e
 #pragma unroll
-        for (int nbk = 0; nbk < 3; ++nbk)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int a = 8 * nbk + 2 * t + e - px;
-            if ((unsigned)a < (unsigned)W) {
-              const float tap = st[ST_WIN + s * LDS + a];
-              v.x += tap * acc[nbk][2 * h + e];
-              v.y += tap * acc[3 + nbk][2 * h + e];
-            }
+        for (int e = 0; e < 2; ++e) {
+          const int c0 = 2 * t + e - px;   // tap index in block 0, in [-15, 7] or <= -9 for an empty row
+          const int nbe = (7 - c0) >> 3;   // block whose tap index is in [0, 8)
+          if (nbe >= 0 && nbe < 3) {
+            const float tap = st[ST_WIN + s * LDS + c0 + 8 * nbe];
+            const float hr = (nbe == 0) ? acc[0][2 * h + e] : (nbe == 1) ? acc[1][2 * h + e] : acc[2][2 * h + e];
+            const float hi = (nbe == 0) ? acc[3][2 * h + e] : (nbe == 1) ? acc[4][2 * h + e] : acc[5][2 * h + e];
+            v.x += tap * hr;
+            v.y += tap * hi;
           }
+        }
         v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
         v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
         v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
