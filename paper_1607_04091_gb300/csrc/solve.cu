@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "gs_internal.h"
@@ -874,21 +875,47 @@ gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const
   for (int i = 0; i < ns; ++i) GS_CUDA(cudaStreamWaitEvent(pool->s[i], pool->start, 0));
   std::vector<char> graphed(B, 0);
   gs_status first = GS_OK;
-  for (int p = 0; p < B; ++p) {
-    cudaStream_t s = pool->s[p % ns];
-    if (graph_solve_ok(plans[p], o)) {
-      gs_status r = launch_solve_graph(plans[p], y[p], x[p], o, s);
-      if (r == GS_OK) {
-        graphed[p] = 1;
-        continue;
+  // largest problems first (samples x coefficients), each on the first stream whose
+  // previous solve has finished: the streams stay busy however the work is spread
+  std::vector<int> ord(B);
+  for (int p = 0; p < B; ++p) ord[p] = p;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    return (double)plans[a]->M * (double)plans[a]->ncoef > (double)plans[b]->M * (double)plans[b]->ncoef;
+  });
+  std::vector<char> busy(ns, 0);
+  int next = 0;
+  while (next < B) {
+    bool launched = false;
+    for (int i = 0; i < ns && next < B; ++i) {
+      if (busy[i]) {
+        const cudaError_t q = cudaEventQuery(pool->done[i]);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return cuda_fail(q, "waiting for a batch stream");
       }
-      if (!plans[p]->solve_graph_failed) return r;
-      cudaGetLastError();
+      const int p = ord[next++];
+      cudaStream_t s = pool->s[i];
+      bool done_graph = false;
+      if (graph_solve_ok(plans[p], o)) {
+        gs_status r = launch_solve_graph(plans[p], y[p], x[p], o, s);
+        if (r == GS_OK) {
+          graphed[p] = 1;
+          done_graph = true;
+        } else {
+          if (!plans[p]->solve_graph_failed) return r;
+          cudaGetLastError();
+        }
+      }
+      if (!done_graph) {
+        gs_solve_info inf;
+        gs_status r = solve(plans[p], y[p], x[p], o, &inf, s);  // host-driven fallback
+        if (infos) infos[p] = inf;
+        if (r != GS_OK && first == GS_OK) first = r;
+      }
+      GS_CUDA(cudaEventRecord(pool->done[i], s));
+      busy[i] = 1;
+      launched = true;
     }
-    gs_solve_info inf;
-    gs_status r = solve(plans[p], y[p], x[p], o, &inf, s);  // host-driven fallback
-    if (infos) infos[p] = inf;
-    if (r != GS_OK && first == GS_OK) first = r;
+    if (!launched) std::this_thread::yield();
   }
   for (int i = 0; i < ns; ++i) {
     GS_CUDA(cudaEventRecord(pool->done[i], pool->s[i]));
