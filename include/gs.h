@@ -65,6 +65,10 @@ typedef struct {
   int sigma;    /* oversampling factor of the NFFT grid, 2 or 4 [2] */
   int direct;   /* 1: evaluate T entry by entry (O(M N^d) per apply, small problems);
                    0: NFFT path; -1: choose (direct when M * N^d <= 2^16) [-1] */
+  int chunk;    /* NFFT path: samples per work item of the spread and interpolation at
+                   most; a tile's samples split into near-equal items (load balance).
+                   > 0: that size; 0: 512; -1: autotune at plan time (times float32
+                   T and T^H for sizes 128..1024 and keeps the fastest) [0] */
 } gs_opts;
 
 /* Build a 1D plan: the representation of T (paper: Freq2Wave(xi, "dbp", J[, bandwidth]),

@@ -87,7 +87,7 @@ static void free_prec_f(PrecData<float>& D) {
     if (p) cudaFree(p);
 }
 static void free_prec_d(PrecData<double>& D) {
-  void* ps[] = {D.frac, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner,
+  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -110,6 +110,50 @@ static void free_plan(Plan* P) {
   }
   free_prec_d(P->d);
   free_prec_f(P->f);
+}
+
+// Work-item size by measurement: for each candidate size the work items are
+// rebuilt and float32 T and T^H (sorted sample order, as inside the solver) are
+// timed back to back; the fastest size stays.  The applies of the chosen plan
+// differ from those of a fixed-size plan only in how the partial sums group.
+static gs_status autotune_chunk(Plan* P, cudaStream_t st) {
+  static const int cand[] = {128, 192, 256, 384, 512, 768, 1024};
+  C<float>* x = P->f.vp;
+  C<float>* y = P->f.vq;
+  GS_CUDA(cudaMemsetAsync(x, 0, P->ncoef * sizeof(C<float>), st));
+  GS_CUDA(cudaMemsetAsync(y, 0, P->M * sizeof(C<float>), st));
+  cudaEvent_t e0, e1;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.0f;
+  gs_status s = GS_OK;
+  for (int c : cand) {
+    s = set_work(P, c, st);
+    if (s != GS_OK) break;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && s == GS_OK; ++rep) {  // rep 0 warms up
+      if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = GS_ECUDA;
+      for (int k = 0; k < (rep ? 3 : 1) && s == GS_OK; ++k) {
+        s = apply_T<float>(P, P->f, x, y, nullptr, st);
+        if (s == GS_OK) s = apply_TH<float>(P, P->f, y, x, nullptr, st);
+      }
+    }
+    if (s != GS_OK) break;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      s = cuda_fail(cudaGetLastError(), "autotune timing");
+      break;
+    }
+    if (best == 0 || ms < best_ms) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != GS_OK) return s;
+  return set_work(P, best, st);
 }
 
 static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, int p, int J,
@@ -142,11 +186,12 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
         set_error("weights[%lld] is negative or not finite", (long long)i);
         return GS_EINVAL;
       }
-  gs_opts o = {8, 4, 2, -1};
+  gs_opts o = {8, 4, 2, -1, 0};
   if (opts) o = *opts;
-  if (o.kb_m_hi < 2 || o.kb_m_hi > 8 || o.kb_m_lo < 2 || o.kb_m_lo > 8 || (o.sigma != 2 && o.sigma != 4)) {
-    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..8), sigma = %d (2 or 4)", o.kb_m_hi, o.kb_m_lo,
-              o.sigma);
+  if (o.kb_m_hi < 2 || o.kb_m_hi > 8 || o.kb_m_lo < 2 || o.kb_m_lo > 8 || (o.sigma != 2 && o.sigma != 4) ||
+      o.chunk < -1 || o.chunk > (1 << 20)) {
+    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..8), sigma = %d (2 or 4), chunk = %d (-1..2^20)",
+              o.kb_m_hi, o.kb_m_lo, o.sigma, o.chunk);
     return GS_EINVAL;
   }
   gs_plan_s* h = new (std::nothrow) gs_plan_s();
@@ -167,9 +212,11 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
   P->m_hi = o.kb_m_hi;
   P->m_lo = o.kb_m_lo;
   P->bandwidth = bandwidth;
+  P->chunk = o.chunk > 0 ? o.chunk : 0;
   if (dims == 2 && ((o.kb_m_hi != 4 && o.kb_m_hi != 6 && o.kb_m_hi != 8) ||
                     (o.kb_m_lo != 4 && o.kb_m_lo != 6 && o.kb_m_lo != 8))) {
     set_error("2D plans take Kaiser-Bessel half-widths 4, 6 or 8 (kb_m_hi = %d, kb_m_lo = %d)", o.kb_m_hi, o.kb_m_lo);
+    delete h;
     return GS_EINVAL;
   }
   int mmax = o.kb_m_hi > o.kb_m_lo ? o.kb_m_hi : o.kb_m_lo;
@@ -204,6 +251,7 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
     GS_CUDA(cudaEventCreateWithFlags(&P->ev_join[i], cudaEventDisableTiming));
   }
   gs_status s = build_plan(P, xi, weights, (cudaStream_t)stream);
+  if (s == GS_OK && o.chunk == -1 && !P->direct) s = autotune_chunk(P, (cudaStream_t)stream);
   if (s != GS_OK) {
     free_plan(P);
     delete h;

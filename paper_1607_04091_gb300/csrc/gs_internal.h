@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gs.h"
 
@@ -128,6 +129,9 @@ struct Plan {
   int32_t* wcol = nullptr;       // work items grouped by bin column (bx), then row
   int32_t* wcol_start = nullptr; // [nbx + 1] offsets into wcol
   int nwork = 0;
+  int chunk = 0;                 // samples per work item at most (near-equal split of a bin)
+  int work_cap = 0;              // work items the partial-sum buffers hold
+  std::vector<int32_t> bin_start_h;  // host copy of bin_start (work lists are rebuilt from it)
   PrecData<double> d;
   PrecData<float> f;
   // FP64 scratch for reductions and solver scalars
@@ -168,6 +172,9 @@ inline gs_status join_aux(Plan* P, cudaStream_t st, int i) {
 
 // implemented in tables.cu
 gs_status build_plan(Plan* P, const double* xi, const double* mu_host, cudaStream_t st);
+// (re)build the work items of every bin with at most `chunk` samples each, and
+// grow the partial-sum buffers to hold them
+gs_status set_work(Plan* P, int chunk, cudaStream_t st);
 // implemented in nfft.cu / direct.cu.  perm != NULL: samples in the caller's
 // order (y[perm[s]]); perm == NULL: samples in the plan's sorted order.
 // norm_part != NULL (2D plans only): the interpolation also writes, per work

@@ -592,18 +592,39 @@ __global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restri
   __syncthreads();
   const int lx = threadIdx.x >> 4, ly = threadIdx.x & 15;
   const int PW = T + 2 * m;
+  // A point takes its own bin and, within m of a tile edge, the neighbour across
+  // that edge (m <= 8 < T: one per axis at most).  Slots in the order of
+  // k_reduce2d_grid: (ya, xa), (ya, xb), (yb, xa), (yb, xb) with ya < yb, xa < xb.
+  const int ya = (ly < m) ? 0 : 1, yb = (ly < m) ? 1 : (ly >= T - m) ? 2 : -1;
+  const int xa = (lx < m) ? 0 : 1, xb = (lx < m) ? 1 : (lx >= T - m) ? 2 : -1;
+  int beg[4], c[4], off[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int iy = (s < 2) ? ya : yb, ix = (s & 1) ? xb : xa;
+    const bool ok = iy >= 0 && ix >= 0;
+    const int j = ok ? iy * 3 + ix : 0;
+    beg[s] = rng[j][0];
+    c[s] = ok ? rng[j][1] - rng[j][0] : 0;
+    off[s] = (lx - T * (ix - 1) + m) * PW + (ly - T * (iy - 1) + m);
+  }
+  const int c01 = c[0] + c[1], c012 = c01 + c[2], K = c012 + c[3];
+  // the contributions k = 0..K-1 in slot order, items ascending: eight loads in
+  // flight, then the adds in k order (the sum of k_reduce2d_grid, bit for bit)
   C<R> acc = mk<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    C<R> v[8];
 #pragma unroll
-  for (int iy = 0; iy < 3; ++iy) {
-    const int qy = ly - T * (iy - 1) + m;
-    if (qy < 0 || qy >= PW) continue;
-#pragma unroll
-    for (int ix = 0; ix < 3; ++ix) {
-      const int qx = lx - T * (ix - 1) + m;
-      if (qx < 0 || qx >= PW) continue;
-      const int r0 = rng[iy * 3 + ix][0], r1 = rng[iy * 3 + ix][1];
-      for (int wi = r0; wi < r1; ++wi) acc = cadd(acc, part[wi * stride + qx * PW + qy]);
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u;
+      const int s = (k >= c[0]) + (k >= c01) + (k >= c012);
+      const int cs = (s == 0) ? 0 : (s == 1) ? c[0] : (s == 2) ? c01 : c012;
+      const int bs = (s == 0) ? beg[0] : (s == 1) ? beg[1] : (s == 2) ? beg[2] : beg[3];
+      const int os = (s == 0) ? off[0] : (s == 1) ? off[1] : (s == 2) ? off[2] : off[3];
+      v[u] = (k < K) ? part[(int64_t)(bs + k - cs) * stride + os] : mk<R>(0, 0);
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < K) acc = cadd(acc, v[u]);
   }
   grid[(int64_t)(bx * T + lx) * n + by * T + ly] = acc;
 }
@@ -616,9 +637,10 @@ __global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restri
 template <typename R>
 __global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const int32_t* __restrict__ wcol,
                                 const int32_t* __restrict__ wcol_start, const C<R>* __restrict__ part,
-                                int64_t stride, int nbx, int tile, int m, int n, int b2, C<R>* __restrict__ side) {
+                                int64_t stride, int nbx, int tile, int m, int n, int b2, int which0,
+                                C<R>* __restrict__ side) {
   __shared__ C<R> red[256];
-  const int which = blockIdx.z, k = blockIdx.y, gb = blockIdx.x;
+  const int which = which0 + (int)blockIdx.z, k = blockIdx.y, gb = blockIdx.x;
   const int pt = threadIdx.x % tile, wl = threadIdx.x / tile, nl = blockDim.x / tile;
   const int g = gb * tile + pt;
   const int PW = tile + 2 * m;
@@ -917,10 +939,14 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
       GS_TRY(fork_aux(P, st, 0));
       GS_TRY(fork_aux(P, st, 1));
       cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
-      dim3 sg(P->nbx, b2, 2);
+      // x-side grids (pass 2) on branch 0; y-side grids and corners (pass 1) on branch 1
+      dim3 sg(P->nbx, b2, 1);
       GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a0,
                 k_reduce2d_side<R><<<sg, 256, 0, a0>>>(P->work_start, P->wcol, P->wcol_start, D.part,
-                                                        D.part_stride, P->nbx, tile, m, n, b2, D.side));
+                                                        D.part_stride, P->nbx, tile, m, n, b2, 0, D.side));
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a1,
+                k_reduce2d_side<R><<<sg, 256, 0, a1>>>(P->work_start, P->wcol, P->wcol_start, D.part,
+                                                        D.part_stride, P->nbx, tile, m, n, b2, 1, D.side));
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), a1,
                 k_reduce_chan<R><<<b2 * b2, 256, 0, a1>>>(D.part, D.part_stride, wsz, b2 * b2, P->nwork,
                                                            D.corner));
@@ -936,8 +962,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
                                                       D.grid));
     if (b2 > 0) {
       GS_CUDA(cudaGetLastError());
-      GS_TRY(join_aux(P, st, 0));
-      GS_TRY(join_aux(P, st, 1));
+      GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
     }
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
@@ -950,6 +975,7 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
+    if (b2 > 0) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
     const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
@@ -1012,7 +1038,7 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
       dim3 sg(P->nbx, b2, 2);
       GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
                 k_reduce2d_side<R><<<sg, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, part,
-                                                        D.part_stride, P->nbx, tile, m, n, b2, D.side));
+                                                        D.part_stride, P->nbx, tile, m, n, b2, 0, D.side));
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
                 k_reduce_chan<R><<<b2 * b2, 256, 0, st>>>(part, D.part_stride, wsz, b2 * b2, P->nwork,
                                                            D.corner));

@@ -358,7 +358,6 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
       int pw = TILE2 + 2 * m;
       D.part_stride = (int64_t)pw * pw + 2 * b2 * pw + b2 * b2;
     }
-    GS_TRY(dalloc(&D.part, (size_t)P->nwork * D.part_stride));
   }
   GS_TRY(dalloc(&D.corner, (size_t)(b2 * b2 > 0 ? b2 * b2 : 1)));
   GS_TRY(dalloc(&D.vx, (size_t)P->ncoef));
@@ -371,6 +370,86 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
 }
 
 }  // namespace
+
+template <typename R>
+static gs_status grow_part(PrecData<R>& D, int nwork) {
+  if (D.part) cudaFree(D.part);
+  D.part = nullptr;
+  return dalloc(&D.part, (size_t)nwork * D.part_stride);
+}
+
+gs_status set_work(Plan* P, int chunk, cudaStream_t st) {
+  if (chunk < 1) {
+    set_error("work item size %d < 1", chunk);
+    return GS_EINVAL;
+  }
+  const std::vector<int32_t>& hstart = P->bin_start_h;
+  // a bin of c samples gives ceil(c / chunk) items of near-equal size, so that
+  // no item is much smaller than its siblings (600 at chunk 512: 300 + 300)
+  std::vector<int32_t> work, wstart(P->nbins + 1);
+  for (int bn = 0; bn < P->nbins; ++bn) {
+    wstart[bn] = (int32_t)(work.size() / 3);
+    const int64_t s0 = hstart[bn], c = hstart[bn + 1] - s0;
+    const int64_t k = (c + chunk - 1) / chunk;
+    for (int64_t i = 0; i < k; ++i) {
+      work.push_back(bn);
+      work.push_back((int32_t)(s0 + c * i / k));
+      work.push_back((int32_t)(s0 + c * (i + 1) / k));
+    }
+  }
+  wstart[P->nbins] = (int32_t)(work.size() / 3);
+  void* old[] = {P->work, P->work_start, P->work_order, P->wcol, P->wcol_start};
+  GS_CUDA(cudaStreamSynchronize(st));
+  for (void* p : old)
+    if (p) cudaFree(p);
+  P->work = P->work_start = P->work_order = P->wcol = P->wcol_start = nullptr;
+  P->nwork = (int)(work.size() / 3);
+  P->chunk = chunk;
+  GS_TRY(dalloc(&P->work, work.size() > 0 ? work.size() : 3));
+  GS_TRY(dalloc(&P->work_start, wstart.size()));
+  if (!work.empty())
+    GS_CUDA(cudaMemcpyAsync(P->work, work.data(), work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemcpyAsync(P->work_start, wstart.data(), wstart.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, st));
+  // launch order: larger items first, so that the last wave holds the short ones
+  std::vector<int32_t> order(P->nwork);
+  for (int i = 0; i < P->nwork; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return work[3 * a + 2] - work[3 * a + 1] > work[3 * b + 2] - work[3 * b + 1];
+  });
+  GS_TRY(dalloc(&P->work_order, order.size() > 0 ? order.size() : 1));
+  if (!order.empty())
+    GS_CUDA(cudaMemcpyAsync(P->work_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            st));
+  // the same work items grouped by bin column (for reductions along x)
+  std::vector<int32_t> wcol, wcs(P->nbx + 1);
+  for (int bx = 0; bx < P->nbx; ++bx) {
+    wcs[bx] = (int32_t)wcol.size();
+    for (int by = 0; by < P->nby; ++by)
+      for (int32_t wi = wstart[by * P->nbx + bx]; wi < wstart[by * P->nbx + bx + 1]; ++wi) wcol.push_back(wi);
+  }
+  wcs[P->nbx] = (int32_t)wcol.size();
+  GS_TRY(dalloc(&P->wcol, wcol.size() > 0 ? wcol.size() : 1));
+  GS_TRY(dalloc(&P->wcol_start, wcs.size()));
+  if (!wcol.empty())
+    GS_CUDA(cudaMemcpyAsync(P->wcol, wcol.data(), wcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemcpyAsync(P->wcol_start, wcs.data(), wcs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  // per-item partial sums of the spread, and the reduction partials (per work
+  // item or 512 blocks, then up to 1184 blocks)
+  if (P->nwork > P->work_cap || !P->red) {
+    const int cap = std::max(P->nwork, 1);
+    if (!P->direct) {
+      GS_TRY(grow_part(P->d, cap));
+      GS_TRY(grow_part(P->f, cap));
+    }
+    if (P->red) cudaFree(P->red);
+    P->red = nullptr;
+    GS_TRY(dalloc(&P->red, (size_t)std::max(8192, cap + 2048)));
+    P->work_cap = cap;
+  }
+  GS_CUDA(cudaStreamSynchronize(st));
+  return GS_OK;
+}
 
 gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cudaStream_t st) {
   const int64_t M = P->M;
@@ -462,52 +541,11 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
   k_gather_fl<<<(M + 255) / 256, 256, 0, st>>>(fl_o, P->perm, M, dims, P->fl);
   GS_CUDA(cudaGetLastError());
 
-  // work items: each bin's sample range split into chunks
-  std::vector<int32_t> hstart(P->nbins + 1);
-  GS_CUDA(cudaMemcpyAsync(hstart.data(), P->bin_start, (P->nbins + 1) * sizeof(int32_t),
+  // work items: each bin's sample range split into chunks (set_work)
+  P->bin_start_h.assign(P->nbins + 1, 0);
+  GS_CUDA(cudaMemcpyAsync(P->bin_start_h.data(), P->bin_start, (P->nbins + 1) * sizeof(int32_t),
                           cudaMemcpyDeviceToHost, st));
   GS_CUDA(cudaStreamSynchronize(st));
-  const int CH = (dims == 1) ? CHUNK1 : CHUNK2;
-  std::vector<int32_t> work, wstart(P->nbins + 1);
-  for (int bn = 0; bn < P->nbins; ++bn) {
-    wstart[bn] = (int32_t)(work.size() / 3);
-    for (int32_t s0 = hstart[bn]; s0 < hstart[bn + 1]; s0 += CH) {
-      work.push_back(bn);
-      work.push_back(s0);
-      work.push_back(std::min(hstart[bn + 1], s0 + CH));
-    }
-  }
-  wstart[P->nbins] = (int32_t)(work.size() / 3);
-  P->nwork = (int)(work.size() / 3);
-  GS_TRY(dalloc(&P->work, work.size()));
-  GS_TRY(dalloc(&P->work_start, wstart.size()));
-  if (!work.empty())
-    GS_CUDA(cudaMemcpyAsync(P->work, work.data(), work.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  GS_CUDA(cudaMemcpyAsync(P->work_start, wstart.data(), wstart.size() * sizeof(int32_t),
-                          cudaMemcpyHostToDevice, st));
-  // launch order: larger items first, so that the last wave holds the short ones
-  std::vector<int32_t> order(P->nwork);
-  for (int i = 0; i < P->nwork; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return work[3 * a + 2] - work[3 * a + 1] > work[3 * b + 2] - work[3 * b + 1];
-  });
-  GS_TRY(dalloc(&P->work_order, order.size()));
-  if (!order.empty())
-    GS_CUDA(cudaMemcpyAsync(P->work_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                            st));
-  // the same work items grouped by bin column (for reductions along x)
-  std::vector<int32_t> wcol, wcs(P->nbx + 1);
-  for (int bx = 0; bx < P->nbx; ++bx) {
-    wcs[bx] = (int32_t)wcol.size();
-    for (int by = 0; by < P->nby; ++by)
-      for (int32_t wi = wstart[by * P->nbx + bx]; wi < wstart[by * P->nbx + bx + 1]; ++wi) wcol.push_back(wi);
-  }
-  wcs[P->nbx] = (int32_t)wcol.size();
-  GS_TRY(dalloc(&P->wcol, wcol.size()));
-  GS_TRY(dalloc(&P->wcol_start, wcs.size()));
-  if (!wcol.empty())
-    GS_CUDA(cudaMemcpyAsync(P->wcol, wcol.data(), wcol.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-  GS_CUDA(cudaMemcpyAsync(P->wcol_start, wcs.data(), wcs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
 
   // per-precision tables and workspaces
   GS_TRY(alloc_prec(P, P->d, P->m_hi));
@@ -523,8 +561,7 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
   k_twiddle<<<(P->n / 2 + 255) / 256, 256, 0, st>>>(P->n, P->d.tw, P->f.tw);
   GS_CUDA(cudaGetLastError());
 
-  // reduction partials: per work item (or 512 blocks), then up to 1184 blocks
-  GS_TRY(dalloc(&P->red, (size_t)std::max(8192, P->nwork + 2048)));
+  GS_TRY(set_work(P, P->chunk > 0 ? P->chunk : (dims == 1 ? CHUNK1 : CHUNK2), st));
   GS_TRY(dalloc(&P->scal, 64));
   GS_TRY(dalloc(&P->flag, 16));
   GS_TRY(dalloc(&P->y64, (size_t)2 * M));

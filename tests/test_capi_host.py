@@ -58,6 +58,10 @@ def test_plan_rejects_nonfinite_xi_and_weights():
     with pytest.raises(gs.GsError) as e:
         gs.gs_plan_2d(np.zeros((10, 2)), 2, 5, stream=_NoStream(), sigma=3)
     assert e.value.status == gs.GS_EINVAL
+    for chunk in (-2, (1 << 20) + 1):  # work-item size: -1 (autotune), 0 (default) or 1..2^20
+        with pytest.raises(gs.GsError) as e:
+            gs.gs_plan_2d(np.zeros((10, 2)), 2, 5, stream=_NoStream(), chunk=chunk)
+        assert e.value.status == gs.GS_EINVAL
 
 
 class _NoStream:

@@ -129,6 +129,29 @@ def test_2d_clustered_center_load_balance():
     check_pair(plan, op, 4**J, xi2.shape[0], gs.GS_FP64, 1e-10, g)
 
 
+@pytest.mark.parametrize("chunk", [1, 37, 128, 4096, -1])
+def test_2d_work_item_sizes(chunk):
+    """Work items of 1 sample up to whole tiles, and the autotuned size: the same
+    operator (float64 to 1e-10, float32 to its tolerance), and the same bits on a
+    second evaluation."""
+    g = synth.rng(15)
+    J = 5
+    xi2 = np.concatenate([g.normal(0, 0.7, size=(3000, 2)), g.uniform(-32, 32, size=(700, 2))])
+    M = xi2.shape[0]
+    op = Operator2D(Basis1D(4, J), xi2)
+    plan = gs.Plan.plan_2d(xi2, 4, J, direct=0, chunk=chunk)
+    check_pair(plan, op, 4**J, M, gs.GS_FP64, 1e-10, g)
+    x = rand_c(g, 4**J)
+    y = rand_c(g, M)
+    tol = tol_for(gs.GS_FP32, 2 * 2**J)
+    a = plan.T(dev(x, gs.GS_FP32), gs.GS_FP32).cpu().numpy()
+    b = plan.TH(dev(y, gs.GS_FP32), gs.GS_FP32).cpu().numpy()
+    assert rel(a, op.apply(x)) < tol
+    assert rel(b, op.adjoint(y)) < tol
+    assert np.array_equal(a, plan.T(dev(x, gs.GS_FP32), gs.GS_FP32).cpu().numpy())
+    assert np.array_equal(b, plan.TH(dev(y, gs.GS_FP32), gs.GS_FP32).cpu().numpy())
+
+
 def test_adjoint_identity_on_gpu():
     g = synth.rng(13)
     J, M = 6, 5000
