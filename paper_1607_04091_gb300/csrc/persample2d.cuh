@@ -622,7 +622,8 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
 // samples, and its element (row s, column k0 + c) is tap k0 + c - pos_s of s,
 // nonzero in exactly one of the three k-steps; each lane loads and splits its
 // taps once per batch and selects them per step.  The item operands G, S0, S1
-// are split once per item into (hi, lo) pairs.  Per batch: cp.async stages the
+// stay plain floats, split at each fragment load (a 64-bit pair load would take
+// two shared-memory wavefronts).  Per batch: cp.async stages the
 // next batch's inputs; warps 0-1 form H (one 16-sample block each, real and
 // imaginary part), warp 2 Q0 and half of RR, warp 3 Q1 and the other half; then
 // four threads per sample combine
@@ -636,14 +637,14 @@ using tc::cp_async4;
 using tc::cp_commit;
 using tc::cp_wait_all;
 constexpr int SBT = 32, W = 8, B2 = 8, TILE = 16, PW = TILE + W;
-constexpr int LDP = 28;  // rows of the (hi, lo) item operands [n][k] in pairs: conflict-free 64-bit fragments
+constexpr int LDQ = 28;  // rows of the item operands [n][k]: conflict-free fragment loads
 constexpr int LDX = 20;  // rows of the corner operands (K = 16), stored [ky][k]
 constexpr int LDS = 20;  // staged rows of 16 floats
-// item operands (floats; the paired planes hold float2 (hi, lo) per element)
-constexpr int I_GR = 0, I_GI = I_GR + 2 * PW * LDP;  // [x][y]
-constexpr int I_S0R = I_GI + 2 * PW * LDP, I_S0I = I_S0R + 2 * B2 * LDP;  // [k][y]
-constexpr int I_S1R = I_S0I + 2 * B2 * LDP, I_S1I = I_S1R + 2 * B2 * LDP;  // [k][x]
-constexpr int I_XR = I_S1I + 2 * B2 * LDP;  // [ky][k]: k < 8 Re X[ky][k], k >= 8 -Im X[ky][k - 8]
+// item operands (floats)
+constexpr int I_GR = 0, I_GI = I_GR + PW * LDQ;  // [x][y]
+constexpr int I_S0R = I_GI + PW * LDQ, I_S0I = I_S0R + B2 * LDQ;  // [k][y]
+constexpr int I_S1R = I_S0I + B2 * LDQ, I_S1I = I_S1R + B2 * LDQ;  // [k][x]
+constexpr int I_XR = I_S1I + B2 * LDQ;  // [ky][k]: k < 8 Re X[ky][k], k >= 8 -Im X[ky][k - 8]
 constexpr int I_XI = I_XR + B2 * LDX;       // [ky][k]: k < 8 Im X[ky][k], k >= 8  Re X[ky][k - 8]
 constexpr int N_ITEM = I_XI + B2 * LDX;
 // the four terms of each sample (interior, x-sides, y-sides, corners), complex
@@ -699,21 +700,6 @@ __device__ inline void win_elems(const float* taps, const int* pos, int rs0, int
       split(v, hi[2 * h + e], lo[2 * h + e]);
     }
 }
-// B fragment (8 x 8) of a paired [n][k] operand
-__device__ inline void frag_b_pair(const float* B, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
-  const int g = lane >> 2, t = lane & 3;
-  const float2 p0 = *reinterpret_cast<const float2*>(B + 2 * ((n0 + g) * LDP + k0 + t));
-  const float2 p1 = *reinterpret_cast<const float2*>(B + 2 * ((n0 + g) * LDP + k0 + t + 4));
-  hi[0] = __float_as_uint(p0.x);
-  lo[0] = __float_as_uint(p0.y);
-  hi[1] = __float_as_uint(p1.x);
-  lo[1] = __float_as_uint(p1.y);
-}
-__device__ inline void put_pair(float* B, int r, int c, float v) {
-  uint32_t h, l;
-  split(v, h, l);
-  *reinterpret_cast<float2*>(B + 2 * (r * LDP + c)) = make_float2(__uint_as_float(h), __uint_as_float(l));
-}
 }  // namespace tci
 
 static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
@@ -737,17 +723,17 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
   for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
     const int r = i / PW, c = i - r * PW;
     const float2 v = grid[(int64_t)((gx0 + r) & nm) * n + ((gy0 + c) & nm)];
-    put_pair(sm + I_GR, r, c, v.x);
-    put_pair(sm + I_GI, r, c, v.y);
+    sm[I_GR + r * LDQ + c] = v.x;
+    sm[I_GI + r * LDQ + c] = v.y;
   }
   for (int i = threadIdx.x; i < B2 * PW; i += blockDim.x) {
     const int k = i / PW, c = i - k * PW;
     const float2 a = side[(int64_t)k * n + ((gy0 + c) & nm)];
     const float2 e = hbuf[(int64_t)bcol(k, b, N) * n + ((gx0 + c) & nm)];
-    put_pair(sm + I_S0R, k, c, a.x);
-    put_pair(sm + I_S0I, k, c, a.y);
-    put_pair(sm + I_S1R, k, c, e.x);
-    put_pair(sm + I_S1I, k, c, e.y);
+    sm[I_S0R + k * LDQ + c] = a.x;
+    sm[I_S0I + k * LDQ + c] = a.y;
+    sm[I_S1R + k * LDQ + c] = e.x;
+    sm[I_S1I + k * LDQ + c] = e.y;
   }
   if (threadIdx.x < B2 * B2) {
     const int kx = threadIdx.x % B2, ky = threadIdx.x / B2;
@@ -809,8 +795,8 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
         }
 #pragma unroll
         for (int nbk = 0; nbk < 3; ++nbk) {
-          frag_b_pair(sm + I_GR, 8 * nbk, 8 * k, lane, bh[0][nbk], bl[0][nbk]);
-          frag_b_pair(sm + I_GI, 8 * nbk, 8 * k, lane, bh[1][nbk], bl[1][nbk]);
+          tc::load_bT(sm + I_GR, LDQ, 8 * nbk, 8 * k, lane, bh[0][nbk], bl[0][nbk]);
+          tc::load_bT(sm + I_GI, LDQ, 8 * nbk, 8 * k, lane, bh[1][nbk], bl[1][nbk]);
         }
 #pragma unroll
         for (int term = 0; term < 3; ++term)
@@ -874,8 +860,8 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
             ah[mb][q] = (ks[i] == k) ? th[i] : 0u;
             al[mb][q] = (ks[i] == k) ? tl[i] : 0u;
           }
-        frag_b_pair(Sr, 0, 8 * k, lane, bh[0], bl[0]);
-        frag_b_pair(Si, 0, 8 * k, lane, bh[1], bl[1]);
+        tc::load_bT(Sr, LDQ, 0, 8 * k, lane, bh[0], bl[0]);
+        tc::load_bT(Si, LDQ, 0, 8 * k, lane, bh[1], bl[1]);
 #pragma unroll
         for (int term = 0; term < 3; ++term)
 #pragma unroll
