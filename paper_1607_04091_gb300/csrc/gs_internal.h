@@ -97,6 +97,8 @@ struct PrecData {
   C<R>* side = nullptr;   // 2D: [2][2b][n]  (0: x-sides along y, 1: y-sides along x)
   C<R>* part = nullptr;   // spread partials, per work item
   C<R>* corner = nullptr; // 2D: (2b)^2 corner adjoint, 1D: 2b boundary adjoint
+  C<R>* hs = nullptr;     // 2D float32: N x n, x transforms of the rows of s (CGNR)
+  C<R>* hp = nullptr;     // 2D float32: N x n, x transforms of the rows of p (CGNR)
   int64_t part_stride = 0;
   // solver vectors (sorted order for M-vectors)
   C<R>* vx = nullptr;  // ncoef
@@ -179,10 +181,13 @@ gs_status set_work(Plan* P, int chunk, cudaStream_t st);
 // order (y[perm[s]]); perm == NULL: samples in the plan's sorted order.
 // norm_part != NULL (2D plans only): the interpolation also writes, per work
 // item i, the sum of |y_s|^2 over its samples to norm_part[i] (nwork values).
-template <typename R> struct PUpdate;
+template <typename R> struct PComb;
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part = nullptr, const PUpdate<R>* pu = nullptr);
+                 double* norm_part = nullptr, const PComb<R>* pc = nullptr);
+// out = x transforms of the coefficient rows of v (N x n), the first pass of T
+template <typename R>
+gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaStream_t st);
 // Solver scalars (float64 slots of Plan::scal) and stop flags (Plan::flag[0]);
 // Plan::flag[FL_ARRIVE] counts the CTAs of a fused CG step that have finished.
 enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
@@ -196,23 +201,35 @@ constexpr int FL_ARRIVE = 4;
 // before that pass (where alpha is computed).
 // With scal != NULL the last CTA to finish also closes the step: it sums the
 // partials in row order into gamma' = ||s||^2 and sets beta = gamma'/gamma, the
-// iteration count and the stop flag (what k_beta_p does otherwise); the p update
-// p = s + beta p then happens in the next forward pass (PUpdate).
+// iteration count and the stop flag (what k_beta_p does otherwise).
+// With hs != NULL the direction of this step is formed here too: before the
+// update, p = s + beta p (beta of the previous step, read before the closing
+// overwrites it) on the interior columns of each row, whose other entries the
+// forward pass updated (PComb); after it, the row's x transform of the new s
+// goes to hs, from which the next forward pass forms that of the next p.
 template <typename R> struct CgStep {
   C<R>* x;
-  const C<R>* p;
+  C<R>* p;
   C<R>* s;
   const double* alpha;
   int* flag;
   double* part;
   int join_branch;
   double* scal;
+  C<R>* hs;
+  const double* beta;
 };
-// p = s + beta p fused into the first forward pass of the next CG step (2D plans);
-// skipped while flag[0] != F_RUN.
-template <typename R> struct PUpdate {
-  C<R>* p;
+// The direction update p = s + beta p of a 2D CGNR step, fused into the forward
+// apply of T p (whose first pass it replaces): the x transform of p is formed
+// from those of s and of the previous p, hp = hs + beta hp (the transform is
+// linear), written back to hp; the x-boundary columns of p (also the corners),
+// which the apply reads as coefficients, become s + beta p in place.  beta = 0
+// takes s alone.  Nothing is written while flag[0] != F_RUN.
+template <typename R> struct PComb {
+  const C<R>* hs;
+  C<R>* hp;
   const C<R>* s;
+  C<R>* p;
   const double* beta;
   const int* flag;
 };
@@ -237,7 +254,7 @@ inline gs_status apply_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
 // per-sample 2D kernels (persample2d_f32.cu / persample2d_f64.cu)
 template <typename R>
 gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                         double* norm_part = nullptr);
+                         double* norm_part = nullptr, const C<R>* hrows = nullptr);  // hrows: row transforms [D.hbuf]
 template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st);
 template <typename R>

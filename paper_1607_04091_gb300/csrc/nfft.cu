@@ -439,16 +439,11 @@ __global__ void k_adj1d_fft(const C<R>* __restrict__ grid, const R* __restrict__
 // pass 1: x-transform of every coefficient row j -> hbuf[j][:]
 template <typename R>
 __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ deap, int N, int n,
-                              int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf,
-                              PUpdate<R> pu) {
+                              int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
-  // fused CG direction update of these rows: p = s + beta p (x is p), every
-  // coefficient of the row visited once below
-  const bool upd = pu.p != nullptr && pu.flag[0] == F_RUN;
-  const R bt = upd ? (R)pu.beta[0] : (R)0;
   // grid point l of row r holds coefficient i = l + N/2 (mod n), deapodised, or 0
   batched<PPT_ROW, C<R>>(
       nr * n,
@@ -457,15 +452,8 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
         const int i = (l + N / 2) & (n - 1);
         C<R> v = mk<R>(0, 0);
         if (i < N) {
-          const int64_t k = (int64_t)(j0 + r) * N + i;
           const R dv = deap[i];
-          C<R> xv = upd ? pu.p[k] : x[k];  // x is p when updating (read through the writable pointer)
-          if (upd) {
-            const C<R> sv = pu.s[k];
-            xv = mk<R>(sv.x + bt * xv.x, sv.y + bt * xv.y);
-            pu.p[k] = xv;
-          }
-          if (dv != (R)0) v = cscale(xv, dv);
+          if (dv != (R)0) v = cscale(x[(int64_t)(j0 + r) * N + i], dv);
         }
         return v;
       },
@@ -480,12 +468,21 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
 template <typename R>
 __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restrict__ x,
                               const R* __restrict__ deap, int N, int n, int logn, int b, int cols,
-                              const C<R>* __restrict__ tw, C<R>* __restrict__ grid, C<R>* __restrict__ side) {
+                              const C<R>* __restrict__ tw, C<R>* __restrict__ grid, C<R>* __restrict__ side,
+                              PComb<R> pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
   const int c0 = blockIdx.x * cols;
   const int ntot = n + 2 * b;
   const int nc = min(cols, ntot - c0);
+  // CG direction update (PComb): every row j < N of each column is visited once
+  // below, the x-boundary rows (deap = 0) included, so that hp and the boundary
+  // columns of p are complete for the interpolation
+  const bool comb = pc.hs != nullptr;
+  const bool wr = comb && pc.flag[0] == F_RUN;
+  const double bd = comb ? pc.beta[0] : 0.0;
+  const bool b0 = bd == 0.0;
+  const R bt = (R)bd;
   // position l of column c holds row j = l + N/2 (mod n) of the column, deapodised, or 0
   batched<PPT_ROW, C<R>>(
       nc * n,
@@ -498,10 +495,30 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
           const int col = c0 + c;
           C<R> u;
           if (col < n) {
-            u = hbuf[(int64_t)j * n + col];
+            const int64_t e = (int64_t)j * n + col;
+            if (comb) {
+              u = pc.hs[e];
+              if (!b0) {
+                const C<R> h = pc.hp[e];
+                u = mk<R>(u.x + bt * h.x, u.y + bt * h.y);
+              }
+              if (wr) pc.hp[e] = u;
+            } else {
+              u = hbuf[e];
+            }
           } else {
             const int k = col - n;
-            u = x[(int64_t)j * N + ((k < b) ? k : (N - 1 - (k - b)))];
+            const int64_t e = (int64_t)j * N + ((k < b) ? k : (N - 1 - (k - b)));
+            if (comb) {
+              u = pc.s[e];
+              if (!b0) {
+                const C<R> q = pc.p[e];
+                u = mk<R>(u.x + bt * q.x, u.y + bt * q.y);
+              }
+              if (wr) pc.p[e] = u;
+            } else {
+              u = x[e];
+            }
           }
           if (dv != (R)0) v = cscale(u, dv);
         }
@@ -767,10 +784,21 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
     __syncthreads();  // also orders this CTA's z stores before the reads below
     if (!run) return;
     const R a = (R)cg.alpha[0];
+    // direction of this step (CgStep::hs): p = s + beta p on the interior columns,
+    // with the beta of the previous step (beta = 0: p = s)
+    const bool dir = cg.hs != nullptr;
+    const double bd = dir ? cg.beta[0] : 0.0;
+    const bool b0 = bd == 0.0;
+    const R bt = (R)bd;
     double acc = 0.0;
     for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
+      const int r = t / N, i = t - r * N;
       const int64_t k = (int64_t)j0 * N + t;
       C<R> xv = cg.x[k], pv = cg.p[k], sv = cg.s[k], zv = z[k];
+      if (dir && i >= b && i < N - b) {
+        pv = b0 ? sv : mk<R>(sv.x + bt * pv.x, sv.y + bt * pv.y);
+        cg.p[k] = pv;
+      }
       xv.x += a * pv.x;
       xv.y += a * pv.y;
       sv.x -= a * zv.x;
@@ -778,6 +806,17 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
       cg.x[k] = xv;
       cg.s[k] = sv;
       acc += (double)sv.x * sv.x + (double)sv.y * sv.y;
+      if (dir) {  // the new s into this row's x-transform input (as k_fwd2d_pass1 lays it out)
+        const R dv = deap[i];
+        const int l = (i - N / 2) & (n - 1);
+        buf[r * n + l] = (dv != (R)0) ? cscale(sv, dv) : mk<R>(0, 0);
+        for (int q = N; q < n; q += N) buf[r * n + ((l + q) & (n - 1))] = mk<R>(0, 0);
+      }
+    }
+    if (dir) {
+      __syncthreads();
+      fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, false);
+      for (int t = threadIdx.x; t < nr * n; t += blockDim.x) cg.hs[(int64_t)j0 * n + t] = buf[t];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -847,8 +886,22 @@ constexpr int FOUR_STEP_N = 4096;  // 1D grids from this size use the two-pass F
 
 // ---------------------------------------------------------------- host drivers
 template <typename R>
+gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaStream_t st) {
+  const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N;
+  const int rows = 1;
+  size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+  gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
+  if (s != GS_OK) return s;
+  GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
+            k_fwd2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(v, D.deap, N, n, logn, rows,
+                                                                                      D.tw, out));
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part, const PUpdate<R>* pu) {
+                 double* norm_part, const PComb<R>* pc) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b;
   const int64_t M = P->M;
   const R beta = (R)D.beta;
@@ -870,22 +923,18 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
               k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
                                                              x, N, M, perm, y));
   } else {
-    const int rows = 1;
-    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
-    gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
-    if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
-              k_fwd2d_pass1<R><<<(N + rows - 1) / rows, fft_threads(rows, n), sh1, st>>>(x, D.deap, N, n, logn, rows, D.tw,
-                                                                        D.hbuf,
-                                                                        pu ? *pu : PUpdate<R>{nullptr, nullptr, nullptr, nullptr}));
+    // pass 1 (the x transforms of the rows), unless a CG direction update forms
+    // them from those of s and of the previous p in pass 2
+    if (!pc) GS_TRY(row_transform<R>(P, D, x, D.hbuf, st));
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
-    s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
+    gs_status s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
-              k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.hbuf, x, D.deap, N, n, logn, b,
-                                                                                cols, D.tw, D.grid, D.side));
-    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part);
+              k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(
+                  D.hbuf, x, D.deap, N, n, logn, b, cols, D.tw, D.grid, D.side,
+                  pc ? *pc : PComb<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}));
+    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part, pc ? pc->hp : nullptr);
     if (si != GS_OK) return si;
   }
   GS_CUDA(cudaGetLastError());
@@ -977,7 +1026,8 @@ gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t
     if (s != GS_OK) return s;
     if (b2 > 0) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
-    const CgStep<R> cgv = cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr};
+    const CgStep<R> cgv =
+        cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr, nullptr, nullptr};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
               k_adj2d_pass1<R><<<(N + rows - 1) / rows, adj1_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
@@ -1059,7 +1109,8 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
                                                                          D.corner, D.deap, N, n, logn, b, rows,
                                                                          D.tw, z, CgStep<R>{nullptr, nullptr, nullptr,
                                                                                             nullptr, nullptr, nullptr,
-                                                                                            -1, nullptr}));
+                                                                                            -1, nullptr, nullptr,
+                                                                                            nullptr}));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
@@ -1079,9 +1130,11 @@ gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t
 }
 
 template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
-                                 double*, const PUpdate<float>*);
+                                 double*, const PComb<float>*);
 template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t,
-                                  double*, const PUpdate<double>*);
+                                  double*, const PComb<double>*);
+template gs_status row_transform<float>(Plan*, PrecData<float>&, const float2*, float2*, cudaStream_t);
+template gs_status row_transform<double>(Plan*, PrecData<double>&, const double2*, double2*, cudaStream_t);
 template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
                                   const CgStep<float>*);
 template gs_status nfft_TH<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*,

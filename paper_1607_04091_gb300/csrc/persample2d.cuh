@@ -957,10 +957,11 @@ gs_status dispatch_wb(int W, int B2, F&& f) {
 
 template <typename R>
 gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                         double* norm_part) {
+                         double* norm_part, const C<R>* hrows) {
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
   if (P->nwork == 0) return GS_OK;
+  const C<R>* hb = hrows ? hrows : D.hbuf;
   return dispatch_wb(2 * D.m, b2, [&](auto wc, auto bc) -> gs_status {
     constexpr int W = decltype(wc)::value;
     constexpr int B2 = decltype(bc)::value;
@@ -972,7 +973,7 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
       GS_LAUNCH("interp2d<f32>", st,
                 k_interp2d_tc<<<P->nwork, 128, shc, st>>>(
                     P->work, P->work_order, P->fl, (const float*)D.win, (const float2*)D.w, (const float2*)D.bf,
-                    (const float2*)D.grid, (const float2*)D.hbuf, (const float2*)D.side, (int)P->n,
+                    (const float2*)D.grid, (const float2*)hb, (const float2*)D.side, (int)P->n,
                     (const float2*)x, (int)P->N, P->M, P->nbx, perm, (float2*)y, norm_part));
       GS_CUDA(cudaGetLastError());
       return GS_OK;
@@ -982,7 +983,7 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
     if (e != GS_OK) return e;
     GS_LAUNCH(pname<R>("interp2d<f32>", "interp2d<f64>"), st,
               k_interp2d<R, W, B2><<<P->nwork, 128, sh, st>>>(P->work, P->work_order, P->fl, D.frac, D.win, D.w, D.bf, b, D.grid,
-                                                              D.hbuf, D.side, (int)P->n, (R)D.beta, x, (int)P->N,
+                                                              hb, D.side, (int)P->n, (R)D.beta, x, (int)P->N,
                                                               P->M, P->nbx, tile, perm, y, norm_part));
     GS_CUDA(cudaGetLastError());
     return GS_OK;

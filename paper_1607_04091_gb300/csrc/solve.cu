@@ -189,7 +189,7 @@ __global__ void k_to32(float2* __restrict__ o, const double2* __restrict__ in, i
 __global__ void k_init_pass(double* scal, int* flag, double thr2, double maxit) {
   scal[S_GAMMA] = scal[S_TMP];
   scal[S_GNEW] = scal[S_TMP];
-  scal[S_BETA] = 0.0;  // the first fused p update leaves p = s
+  scal[S_BETA] = 0.0;  // the first direction of a pass is p = s
   flag[FL_ARRIVE] = 0;
   scal[S_S0] = scal[S_TMP];
   scal[S_THR2] = thr2;
@@ -235,13 +235,16 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
   // q = T p with ||q||^2 partials: per work item from the 2D interpolation, else a grid reduction
   int np = RED_BLOCKS;
   gs_status s;
-  // 2D CGNR: the step is closed by the adjoint's last pass and p = s + beta p is
-  // applied by the next forward pass (no separate beta / p kernel)
+  // 2D CGNR: the step is closed by the adjoint's last pass (no separate beta / p
+  // kernel), and p = s + beta p is formed where it is read: its x transform in the
+  // forward column pass (from those of s and of the previous p, so that T p needs
+  // no row pass), its boundary columns there too, its interior columns in the
+  // adjoint's last pass, which also transforms the rows of the new s
   const bool fused = normal_eq && !P->direct && P->dims == 2;
   if (!P->direct && P->dims == 2) {
     np = P->nwork;
-    const PUpdate<R> pu{D.vp, D.vs, P->scal + S_BETA, P->flag};
-    s = nfft_T<R>(P, D, D.vp, D.vq, nullptr, st, P->red, fused ? &pu : nullptr);
+    const PComb<R> pc{D.hs, D.hp, D.vs, D.vp, P->scal + S_BETA, P->flag};
+    s = nfft_T<R>(P, D, D.vp, D.vq, nullptr, st, P->red, fused ? &pc : nullptr);
     if (s != GS_OK) return s;
   } else {
     s = apply_T<R>(P, D, D.vp, D.vq, nullptr, st);
@@ -260,7 +263,7 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
     GS_CUDA(cudaGetLastError());
     if (!P->direct && P->dims == 2) {
       // 2D: the x and s update runs in the adjoint's last pass, one partial per coefficient row
-      const CgStep<R> cg{D.vx, D.vp, D.vs, P->scal + S_ALPHA, P->flag, red_s, 2, P->scal};
+      const CgStep<R> cg{D.vx, D.vp, D.vs, P->scal + S_ALPHA, P->flag, red_s, 2, P->scal, D.hs, P->scal + S_BETA};
       GS_TRY(nfft_TH<R>(P, D, D.vq, D.vz, nullptr, st, &cg));
       np_s = (int)P->N;
     } else {
@@ -357,6 +360,7 @@ gs_status cgls_pass(Plan* P, PrecData<R>& D, double thr2, int maxit, int check, 
   const int64_t nc = P->ncoef;
   GS_CUDA(cudaMemsetAsync(D.vx, 0, nc * sizeof(C<R>), st));
   GS_LAUNCH("solve_copy", st, k_copy<R><<<grid_for(nc), 256, 0, st>>>(D.vp, D.vs, nc));
+  if (normal_eq && !P->direct && P->dims == 2) GS_TRY(row_transform<R>(P, D, D.vs, D.hs, st));
   GS_LAUNCH("solve_init_pass", st, k_init_pass<<<1, 1, 0, st>>>(P->scal, P->flag, thr2, (double)maxit));
   GS_CUDA(cudaGetLastError());
   int hflag = F_RUN;
@@ -496,7 +500,7 @@ __global__ void k_pass_init(double* scal, int* flag) {
                                     scal[G_OUTER] == 0.0 && scal[G_WARM] != 0.0);
   scal[S_GAMMA] = ns2;
   scal[S_GNEW] = ns2;
-  scal[S_BETA] = 0.0;  // the first fused p update leaves p = s
+  scal[S_BETA] = 0.0;  // the first direction of a pass is p = s
   flag[FL_ARRIVE] = 0;
   scal[S_S0] = ns2;
   scal[S_THR2] = thr;
@@ -631,6 +635,7 @@ gs_status build_solve_graph(Plan* P, bool with_x0, cudaStream_t st, cudaGraphExe
     k_pass_init<<<1, 1, 0, c>>>(P->scal, P->flag);
     GS_CUDA(cudaMemsetAsync(F.vx, 0, nc * sizeof(float2), c));
     k_copy<float><<<grid_for(nc), 256, 0, c>>>(F.vp, F.vs, nc);
+    if (!P->direct && P->dims == 2) GS_TRY(row_transform<float>(P, F, F.vs, F.hs, c));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   }, &n_pinit));
