@@ -184,7 +184,7 @@ gs_status set_work(Plan* P, int chunk, cudaStream_t st);
 template <typename R> struct PComb;
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part = nullptr, const PComb<R>* pc = nullptr);
+                 double* norm_part = nullptr, const PComb<R>* pc = nullptr, bool df = false);
 // out = x transforms of the coefficient rows of v (N x n), the first pass of T
 template <typename R>
 gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaStream_t st);
@@ -254,7 +254,8 @@ inline gs_status apply_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
 // per-sample 2D kernels (persample2d_f32.cu / persample2d_f64.cu)
 template <typename R>
 gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                         double* norm_part = nullptr, const C<R>* hrows = nullptr);  // hrows: row transforms [D.hbuf]
+                         double* norm_part = nullptr, const C<R>* hrows = nullptr,  // hrows: row transforms [D.hbuf]
+                         bool df = false);  // float64: double-float arithmetic (k_interp2d_df)
 template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st);
 template <typename R>

@@ -901,7 +901,7 @@ gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaS
 
 template <typename R>
 gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
-                 double* norm_part, const PComb<R>* pc) {
+                 double* norm_part, const PComb<R>* pc, bool df) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b;
   const int64_t M = P->M;
   const R beta = (R)D.beta;
@@ -934,7 +934,7 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
               k_fwd2d_pass2<R><<<(n + 2 * b + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(
                   D.hbuf, x, D.deap, N, n, logn, b, cols, D.tw, D.grid, D.side,
                   pc ? *pc : PComb<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}));
-    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part, pc ? pc->hp : nullptr);
+    gs_status si = launch_interp2d<R>(P, D, x, y, perm, st, norm_part, pc ? pc->hp : nullptr, df);
     if (si != GS_OK) return si;
   }
   GS_CUDA(cudaGetLastError());
@@ -1130,9 +1130,9 @@ gs_status scatter_user(Plan* P, const C<R>* y_sorted, C<R>* y_user, cudaStream_t
 }
 
 template gs_status nfft_T<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
-                                 double*, const PComb<float>*);
+                                 double*, const PComb<float>*, bool);
 template gs_status nfft_T<double>(Plan*, PrecData<double>&, const double2*, double2*, const int32_t*, cudaStream_t,
-                                  double*, const PComb<double>*);
+                                  double*, const PComb<double>*, bool);
 template gs_status row_transform<float>(Plan*, PrecData<float>&, const float2*, float2*, cudaStream_t);
 template gs_status row_transform<double>(Plan*, PrecData<double>&, const double2*, double2*, cudaStream_t);
 template gs_status nfft_TH<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,

@@ -3,6 +3,6 @@
 
 namespace gs {
 template gs_status launch_interp2d<float>(Plan*, PrecData<float>&, const float2*, float2*, const int32_t*, cudaStream_t,
-                                           double*, const float2*);
+                                           double*, const float2*, bool);
 template gs_status launch_spread2d<float>(Plan*, PrecData<float>&, const float2*, const int32_t*, float2*, cudaStream_t);
 }  // namespace gs

@@ -414,9 +414,14 @@ __global__ void k_addto(double2* __restrict__ x, const C<R>* __restrict__ d, int
   }
 }
 
-// r64 = y64 - T x64 (float64 forward apply)
+// r64 = y64 - T x64: the forward apply from float64 data, its interpolation in
+// double-float arithmetic (accurate to ~1e-13, far below what the refinement
+// needs)
 gs_status residual64(Plan* P, cudaStream_t st) {
-  GS_TRY(apply_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, st));
+  if (P->direct)
+    GS_TRY(direct_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, st));
+  else
+    GS_TRY(nfft_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, st, nullptr, nullptr, true));
   GS_LAUNCH("solve_sub64", st, k_sub64<<<grid_for(P->M), 256, 0, st>>>((double2*)P->r64, (const double2*)P->y64, P->d.vq, P->M));
   GS_CUDA(cudaGetLastError());
   return GS_OK;

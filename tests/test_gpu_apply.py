@@ -152,6 +152,29 @@ def test_2d_work_item_sizes(chunk):
     assert np.array_equal(b, plan.TH(dev(y, gs.GS_FP32), gs.GS_FP32).cpu().numpy())
 
 
+@pytest.mark.parametrize("p, clustered", [(4, False), (4, True), (2, False), (1, False)])
+def test_2d_float64_apply_in_double_float(monkeypatch, p, clustered):
+    """The float64 forward apply with its interpolation in double-float arithmetic
+    (the refinement residual's apply; GS_DF64 routes every float64 apply there):
+    within the float64 tolerance of the oracle and within 1e-12 of the float64
+    kernel, for db4, db2 and Haar (no boundary columns)."""
+    g = synth.rng(16)
+    J = 5
+    if clustered:
+        xi2 = np.concatenate([g.normal(0, 0.7, size=(3000, 2)), g.uniform(-32, 32, size=(700, 2))])
+    else:
+        xi2 = g.uniform(-40, 40, size=(2500, 2))
+    op = Operator2D(Basis1D(p, J), xi2)
+    plan = gs.Plan.plan_2d(xi2, p, J, direct=0)
+    x = rand_c(g, 4**J)
+    monkeypatch.delenv("GS_DF64", raising=False)
+    y64 = plan.T(dev(x, gs.GS_FP64), gs.GS_FP64).cpu().numpy()
+    monkeypatch.setenv("GS_DF64", "1")
+    ydf = plan.T(dev(x, gs.GS_FP64), gs.GS_FP64).cpu().numpy()
+    assert rel(ydf, op.apply(x)) < 1e-10
+    assert rel(ydf, y64) < 1e-12
+
+
 def test_adjoint_identity_on_gpu():
     g = synth.rng(13)
     J, M = 6, 5000
