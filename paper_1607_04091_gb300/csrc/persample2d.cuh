@@ -496,7 +496,7 @@ constexpr int LDO = 24;  // rows of the window operands: 24 grid offsets (confli
                          // which only reach output rows >= 24, never stored
 constexpr int LDT = 36;  // boundary operands stored transposed, [k][sample]: conflict-free
                          // writes (one lane per sample) and fragment loads
-constexpr int LDS = 20;  // staged rows of 16 floats (conflict-free float4 reads)
+constexpr int LDS = 16;  // staged rows of 16 floats, 16-byte chunks swizzled (see srow)
 // operand area (floats)
 constexpr int O_AR = 0, O_AI = O_AR + SBT * LDO, O_BX = O_AI + SBT * LDO, O_BY = O_BX + SBT * LDO;
 constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + B2 * LDT, O_V1R = O_V0I + B2 * LDT;
@@ -556,6 +556,10 @@ __device__ inline void load_aT(const float* A, int ld, int m0, int k0, int lane,
   split(A[(m0 + g) * ld + k0 + t + 4], hi[2], lo[2]);
   split(A[(m0 + g + 8) * ld + k0 + t + 4], hi[3], lo[3]);
 }
+// float offset of 16-byte chunk c (0..3) of staged row j: chunks XOR-swizzled by
+// (j >> 1) & 3, so that eight consecutive rows reading (or writing) the same chunk
+// hit eight distinct 4-bank groups
+__device__ inline int srow(int j, int c) { return j * LDS + 4 * (c ^ ((j >> 1) & 3)); }
 // B fragment from an operand stored [n][k]
 __device__ inline void load_bT(const float* B, int ld, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
   const int g = lane >> 2, t = lane & 3;
@@ -589,12 +593,12 @@ __device__ inline void stage(float* sm, int wid, int lane, int sb, int nb, const
   if (wid == 0) {
     const float* src = win + s * (2 * W);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) cp_async16(sm + S_WIN + lane * LDS + 4 * c, src + 4 * c);
+    for (int c = 0; c < 4; ++c) cp_async16(sm + S_WIN + srow(lane, c), src + 4 * c);
   } else if (wid < 3) {
     const float2* src = bf + (s + (wid == 2 ? M : 0)) * B2;
-    float* dst = sm + (wid == 1 ? S_BX : S_BY) + lane * LDS;
+    float* dst = sm + (wid == 1 ? S_BX : S_BY);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) cp_async16(dst + 4 * c, src + 2 * c);
+    for (int c = 0; c < 4; ++c) cp_async16(dst + srow(lane, c), src + 2 * c);
   } else {
     cp_async8(sm + S_W + 4 * lane, w + s);
     cp_async8(sm + S_W + 4 * lane + 2, w + M + s);
@@ -659,8 +663,9 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         const float2 us = *reinterpret_cast<const float2*>(st + S_U + 2 * j);
         const int* flj = reinterpret_cast<const int*>(st + S_FL + 2 * j);
         const int pos = (wid == 3) ? flj[1] - oy + 1 : flj[0] - ox + 1;
-        const float* tp = st + S_WIN + j * LDS + (wid == 3 ? W : 0);
-        const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
+        const int cb = (wid == 3) ? 2 : 0;  // chunks of the y taps (8..15) or x taps (0..7)
+        const float4 t0 = *reinterpret_cast<const float4*>(st + S_WIN + srow(j, cb));
+        const float4 t1 = *reinterpret_cast<const float4*>(st + S_WIN + srow(j, cb + 1));
         const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         float scale = 1.0f;
         if (wid < 2) {
@@ -671,11 +676,11 @@ static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
         for (int a = 0; a < W; ++a) row[pos + a] = scale * tap[a];
         prev = pos;
         // boundary operands: warp 0 V0 (x-sides), 1 V1 (y-sides), 2 A = u conj(bx), 3 conj(by)
-        const float* bp = st + ((wid == 0 || wid == 2) ? S_BX : S_BY) + j * LDS;
+        const float* bp = st + ((wid == 0 || wid == 2) ? S_BX : S_BY);
         const float2 uwx = cmulc(us, wxs), uwy = cmulc(us, wys);
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          const float4 f = *reinterpret_cast<const float4*>(bp + 4 * h);
+          const float4 f = *reinterpret_cast<const float4*>(bp + srow(j, h));
           const float2 bk[2] = {make_float2(f.x, f.y), make_float2(f.z, f.w)};
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
