@@ -71,3 +71,23 @@ def test_2d_db4_solve_matches_oracle_cgls(mode):
     assert info["status"] == gs.GS_OK, info
     assert rel(x.cpu().numpy(), xo) < (1e-9 if mode == gs.GS_SOLVE_FP64 else 1e-8)
     assert rel(x.cpu().numpy(), xt) < 1e-8  # consistent data: exact recovery
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_2d_mixed_solve_other_boundary_widths(p):
+    """Mixed solves of 2D Haar (no boundary columns) and db2 (2b = 4): the fused
+    CG step, which updates the boundary columns of the direction in the forward
+    pass and the interior ones in the adjoint's last pass, reaches the oracle's
+    CGLS solution."""
+    g = synth.rng(1004 + p)
+    J = 4
+    N = 2**J
+    xi2 = synth.jitter_2d(2 * N, g)
+    op = Operator2D(Basis1D(p, J), xi2)
+    xt = synth.ellipse_phantom(N, g) + 0j
+    y = op.apply(xt)
+    xo, it, _ = cgls(op.apply, op.adjoint, y, tol=1e-13, maxit=3000)
+    plan = gs.Plan.plan_2d(xi2, p, J, direct=0)
+    x, info = plan.solve(dev(y), tol=1e-11, mode=gs.GS_SOLVE_MIXED, maxit=3000)
+    assert info["status"] == gs.GS_OK, info
+    assert rel(x.cpu().numpy(), xo) < 1e-8
