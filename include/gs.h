@@ -121,9 +121,12 @@ typedef enum {
   GS_SOLVE_FP64 = 0,  /* textbook CGLS with GS_FP64 applies throughout */
   GS_SOLVE_MIXED = 1  /* iterative refinement: x += d, d from a CG pass on the normal
                          equations T^H T d = T^H r with GS_FP32 applies and float64
-                         scalars; r = y - T x with a GS_FP64 forward apply between
-                         passes; T^H r (the pass rhs and the stop test) with a GS_FP32
-                         adjoint when tol >= 1e-7, else GS_FP64 */
+                         scalars; r = y - T x with a forward apply from float64 data
+                         between passes (2D NFFT plans: its interpolation in
+                         double-float arithmetic, ~1e-13 relative); T^H r (the pass
+                         rhs and the stop test) with a GS_FP32 adjoint when
+                         tol >= 1e-7, else GS_FP64.  Data and coefficients must stay
+                         within the float32 range (|values| < 1e38). */
 } gs_solve_mode;
 
 typedef struct {
