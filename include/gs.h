@@ -29,6 +29,16 @@
  *   - Errors are returned as gs_status; gs_last_error_detail() gives a
  *     thread-local description.  Nothing aborts or throws across the ABI.
  *   - A plan is not thread-safe: do not run two calls on one plan concurrently.
+ *
+ * Environment switches (diagnostics and tests; leave them unset in normal use)
+ *   GS_NO_TC      2D float32 spread and interpolation run the scalar kernels
+ *                 instead of the tensor-core ones (read at every launch)
+ *   GS_DF64       every 2D float64 forward apply interpolates in double-float
+ *                 arithmetic, not only the refinement residual's (read at every
+ *                 launch)
+ *   GS_NO_GRAPHS  solves launch their kernels one by one instead of through
+ *                 captured CUDA graphs (read once per process)
+ *   Results agree within the tolerances stated at each entry point either way.
  */
 #ifndef GS_H
 #define GS_H
@@ -112,8 +122,10 @@ gs_status gs_apply_TH(gs_plan plan, int precision, const void* y, void* x, void*
  * (GS_EUNSUPPORTED for direct mode); GS_EINVAL when the plan's scratch exceeds
  * 8 MiB (nwork * part_stride complex values).  All calls share the array, so
  * calls whose GPU work overlaps race: order them on one stream.  The first call
- * on a device looks up the array address (cudaGetSymbolAddress); make it before
- * any stream capture.  Buffers as gs_apply_TH. */
+ * on a device looks up the array address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process; make that first call before any stream capture.  The
+ * kept address, like every plan, does not survive cudaDeviceReset (or any other
+ * destruction of the device's primary context).  Buffers as gs_apply_TH. */
 gs_status gs_apply_TH_noalloc(gs_plan plan, int precision, const void* y, void* x, void* stream);
 
 /* Solver settings for gs_solve. */
@@ -153,6 +165,8 @@ typedef struct {
 
 /* Weighted least squares x = argmin ||T x - y|| (Sec. 2, eq. least_squares; the
  * paper's T \ y, Sec. 6.2) by CGLS, stopped on the normal-equation residual.
+ * GS_EINVAL unless the plan has more samples than coefficients (M > N^d: Sec. 2
+ * takes N < M for a stable reconstruction); applies accept any M >= 1.
  *   y    device, M complex128 (weighted data)
  *   x    device, ncoef complex128; the solution (and the start if x0_given)
  *   info host, may be NULL

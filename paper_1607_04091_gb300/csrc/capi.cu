@@ -343,6 +343,12 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
     set_error("bad solve options (tol > 0, maxit >= 1, mode 0/1, max_outer >= 1, 0 < inner_rtol < 1)");
     return GS_EINVAL;
   }
+  if (plan->P.M <= plan->P.ncoef) {
+    // Sec. 2: the least-squares reconstruction needs more samples than coefficients
+    set_error("gs_solve: M = %lld samples must exceed the %lld coefficients (stable sampling, Sec. 2)",
+              (long long)plan->P.M, (long long)plan->P.ncoef);
+    return GS_EINVAL;
+  }
   return solve(&plan->P, (const double*)y, (double*)x, o, info, (cudaStream_t)stream);
 }
 
@@ -447,6 +453,11 @@ gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void
       return GS_EINVAL;
     }
     ps[i] = &plans[i]->P;
+    if (ps[i]->M <= ps[i]->ncoef) {
+      set_error("plans[%d]: M = %lld samples must exceed the %lld coefficients (stable sampling, Sec. 2)", i,
+                (long long)ps[i]->M, (long long)ps[i]->ncoef);
+      return GS_EINVAL;
+    }
     ys[i] = (const double*)y[i];
     xs[i] = (double*)x[i];
   }

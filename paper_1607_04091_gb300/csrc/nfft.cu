@@ -941,107 +941,12 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
   return GS_OK;
 }
 
+// The adjoint with the spread's per-work-item partial sums (nwork x part_stride)
+// in `part`: the plan's own buffer (nfft_TH) or a caller-given one
+// (nfft_TH_scratch, which allocates nothing).
 template <typename R>
-gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,
-                  const CgStep<R>* cg) {
-  const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
-  const R beta = (R)D.beta;
-  const int m = D.m, tile = P->tile;
-  if (P->nwork == 0) {
-    GS_CUDA(cudaMemsetAsync(z, 0, P->ncoef * sizeof(C<R>), st));
-    return GS_OK;
-  }
-  if (P->dims == 1) {
-    const int warps = 4;
-    size_t sh = (size_t)warps * (tile + 2 * m + b2) * sizeof(C<R>);
-    GS_LAUNCH(pname<R>("spread1d<f32>", "spread1d<f64>"), st,
-              k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile,
-                                                              m, beta, D.part, D.part_stride));
-    GS_LAUNCH(pname<R>("reduce1d<f32>", "reduce1d<f64>"), st,
-              k_reduce1d<R><<<(n + 127) / 128, 128, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m,
-                                                             n, D.grid));
-    if (b2 > 0)
-      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
-                k_reduce_chan<R><<<b2, 256, 0, st>>>(D.part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
-    if (n >= FOUR_STEP_N) {
-      const int logn1 = logn / 2, logn2 = logn - logn1, n1 = 1 << logn1, n2 = 1 << logn2;
-      GS_LAUNCH(pname<R>("adj1d_rows<f32>", "adj1d_rows<f64>"), st,
-                k_adj1d_rows<R><<<n2, 256, n1 * sizeof(C<R>), st>>>(D.grid, n, n1, logn1, n2, D.tw, D.ftmp));
-      GS_LAUNCH(pname<R>("adj1d_cols<f32>", "adj1d_cols<f64>"), st,
-                k_adj1d_cols<R><<<n1, 256, n2 * sizeof(C<R>), st>>>(D.ftmp, D.deap, N, n, n1, n2, logn2, D.tw,
-                                                                    D.corner, b, z));
-    } else {
-      size_t shf = (size_t)n * sizeof(C<R>);
-      gs_status s = set_smem<R>((const void*)k_adj1d_fft<R>, shf);
-      if (s != GS_OK) return s;
-      GS_LAUNCH(pname<R>("adj1d_fft<f32>", "adj1d_fft<f64>"), st,
-                k_adj1d_fft<R><<<1, fft_threads(1, n), shf, st>>>(D.grid, D.deap, N, n, logn, D.tw, D.corner, b, z));
-    }
-  } else {
-    const int PW = tile + 2 * m;
-    const int wsz = PW * PW + 2 * b2 * PW;
-    gs_status s = launch_spread2d<R>(P, D, y, perm, D.part, st);
-    if (s != GS_OK) return s;
-    // the three reductions of the partials read the same input: side segments and
-    // corners on two side branches, the grid on st
-    if (b2 > 0) {
-      GS_TRY(fork_aux(P, st, 0));
-      GS_TRY(fork_aux(P, st, 1));
-      cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
-      // x-side grids (pass 2) on branch 0; y-side grids and corners (pass 1) on branch 1
-      dim3 sg(P->nbx, b2, 1);
-      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a0,
-                k_reduce2d_side<R><<<sg, 256, 0, a0>>>(P->work_start, P->wcol, P->wcol_start, D.part,
-                                                        D.part_stride, P->nbx, tile, m, n, b2, 0, D.side));
-      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a1,
-                k_reduce2d_side<R><<<sg, 256, 0, a1>>>(P->work_start, P->wcol, P->wcol_start, D.part,
-                                                        D.part_stride, P->nbx, tile, m, n, b2, 1, D.side));
-      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), a1,
-                k_reduce_chan<R><<<b2 * b2, 256, 0, a1>>>(D.part, D.part_stride, wsz, b2 * b2, P->nwork,
-                                                           D.corner));
-    }
-    dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    if (tile == 16 && P->nbx >= 3)
-      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
-                k_reduce2d_grid16<R><<<rg, 256, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, m, n,
-                                                         D.grid));
-    else
-      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
-                k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, D.part, D.part_stride, P->nbx, tile, m, n,
-                                                      D.grid));
-    if (b2 > 0) {
-      GS_CUDA(cudaGetLastError());
-      GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
-    }
-    const int cols = pass_cols<R>();
-    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
-    s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
-    if (s != GS_OK) return s;
-    GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
-              k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
-                                                                              cols, D.tw, D.hbuf, z));
-    const int rows = 1;
-    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
-    s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
-    if (s != GS_OK) return s;
-    if (b2 > 0) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
-    if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
-    const CgStep<R> cgv =
-        cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr, nullptr, nullptr};
-    GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
-              k_adj2d_pass1<R><<<(N + rows - 1) / rows, adj1_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
-                                                                         D.corner, D.deap, N, n, logn, b, rows,
-                                                                         D.tw, z, cgv));
-  }
-  GS_CUDA(cudaGetLastError());
-  return GS_OK;
-}
-
-// The adjoint of nfft_TH with the spread's per-work-item partial sums in a
-// caller-given buffer `part` (nwork x part_stride) instead of the plan's.
-template <typename R>
-gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
-                          cudaStream_t st) {
+static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
+                              cudaStream_t st, const CgStep<R>* cg) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N, b = P->b, b2 = 2 * b;
   const R beta = (R)D.beta;
   const int m = D.m, tile = P->tile;
@@ -1080,18 +985,36 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     const int wsz = PW * PW + 2 * b2 * PW;
     gs_status s = launch_spread2d<R>(P, D, y, perm, part, st);
     if (s != GS_OK) return s;
-    dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
-              k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m, n,
-                                                    D.grid));
+    // the three reductions of the partials read the same input: side segments and
+    // corners on two side branches, the grid on st
     if (b2 > 0) {
-      dim3 sg(P->nbx, b2, 2);
-      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), st,
-                k_reduce2d_side<R><<<sg, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, part,
+      GS_TRY(fork_aux(P, st, 0));
+      GS_TRY(fork_aux(P, st, 1));
+      cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
+      // x-side grids (pass 2) on branch 0; y-side grids and corners (pass 1) on branch 1
+      dim3 sg(P->nbx, b2, 1);
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a0,
+                k_reduce2d_side<R><<<sg, 256, 0, a0>>>(P->work_start, P->wcol, P->wcol_start, part,
                                                         D.part_stride, P->nbx, tile, m, n, b2, 0, D.side));
-      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
-                k_reduce_chan<R><<<b2 * b2, 256, 0, st>>>(part, D.part_stride, wsz, b2 * b2, P->nwork,
+      GS_LAUNCH(pname<R>("reduce2d_side<f32>", "reduce2d_side<f64>"), a1,
+                k_reduce2d_side<R><<<sg, 256, 0, a1>>>(P->work_start, P->wcol, P->wcol_start, part,
+                                                        D.part_stride, P->nbx, tile, m, n, b2, 1, D.side));
+      GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), a1,
+                k_reduce_chan<R><<<b2 * b2, 256, 0, a1>>>(part, D.part_stride, wsz, b2 * b2, P->nwork,
                                                            D.corner));
+    }
+    dim3 rg(P->nbx, P->nby), rb(tile, tile);
+    if (tile == 16 && P->nbx >= 3)
+      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+                k_reduce2d_grid16<R><<<rg, 256, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, m, n,
+                                                         D.grid));
+    else
+      GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
+                k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m, n,
+                                                      D.grid));
+    if (b2 > 0) {
+      GS_CUDA(cudaGetLastError());
+      GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
     }
     const int cols = pass_cols<R>();
     size_t sh2 = (size_t)cols * n * sizeof(C<R>);
@@ -1104,16 +1027,28 @@ gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
+    if (b2 > 0) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
+    if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
+    const CgStep<R> cgv =
+        cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr, nullptr, nullptr};
     GS_LAUNCH(pname<R>("adj2d_pass1<f32>", "adj2d_pass1<f64>"), st,
               k_adj2d_pass1<R><<<(N + rows - 1) / rows, adj1_threads(rows, n), sh1, st>>>(D.hbuf, D.side + (int64_t)b2 * n,
                                                                          D.corner, D.deap, N, n, logn, b, rows,
-                                                                         D.tw, z, CgStep<R>{nullptr, nullptr, nullptr,
-                                                                                            nullptr, nullptr, nullptr,
-                                                                                            -1, nullptr, nullptr,
-                                                                                            nullptr}));
+                                                                         D.tw, z, cgv));
   }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
+}
+
+template <typename R>
+gs_status nfft_TH(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, cudaStream_t st,
+                  const CgStep<R>* cg) {
+  return nfft_TH_part<R>(P, D, y, z, perm, D.part, st, cg);
+}
+template <typename R>
+gs_status nfft_TH_scratch(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, const int32_t* perm, C<R>* part,
+                          cudaStream_t st) {
+  return nfft_TH_part<R>(P, D, y, z, perm, part, st, nullptr);
 }
 
 template <typename R>

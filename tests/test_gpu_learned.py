@@ -2,10 +2,10 @@
 
 A residual CNN is trained by the library's kernels on pairs the method itself
 produced (T^H y, CGLS solution) for a 32 x 32 db4 radial problem; on held-out
-data the learned start must not need more CGLS iterations to the 1e-6
-tolerance than the zero start, and every solve must meet the tolerance by the
-oracle's FP64 residual.  Reported numbers: mean iterations from zero, from the
-adjoint (untrained net) and from the trained net.
+data the learned start must need at least 10% fewer CGLS iterations to the
+1e-6 tolerance than both starts without the network -- from zero and from the
+density-compensated adjoint u = T^H y (the untrained, identity net) -- and every
+solve must meet the tolerance by the oracle's FP64 residual.
 """
 import numpy as np
 import pytest
@@ -68,4 +68,6 @@ def test_learned_start_gain():
             its[key].append(info["iterations"])
     mean = {k: float(np.mean(v)) for k, v in its.items()}
     print("mean CGLS iterations to 1e-6:", mean)
-    assert mean["learned"] <= mean["zero"]
+    msg = f"mean CGLS iterations to 1e-6: {mean}"
+    assert mean["learned"] <= 0.9 * mean["adjoint"], msg
+    assert mean["learned"] <= 0.9 * mean["zero"], msg

@@ -265,6 +265,31 @@ def test_voronoi_1d():
     assert abs(w.sum() - 16.0) < 1e-12 and np.all(w > 0)
 
 
+def test_voronoi_1d_hand_worked_unsorted():
+    # Sec. 4.1: the weight of xi_m is the length of its Voronoi cell in [-K, K].
+    # Sorted: -4, -1, 0.5, 2, 3, 6; midpoints -2.5, -0.25, 1.25, 2.5, 4.5; cells
+    # [-5,-2.5] [-2.5,-0.25] [-0.25,1.25] [1.25,2.5] [2.5,4.5] [4.5,5] (6 lies
+    # beyond K = 5: only the part of its cell inside [-K, K] counts).  Listed in
+    # the caller's (unsorted) order:
+    xi = np.array([3.0, -1.0, 0.5, -4.0, 2.0, 6.0])
+    want = np.array([2.0, 2.25, 1.5, 2.5, 1.25, 0.5])
+    assert np.array_equal(voronoi_1d(xi, 5.0), want)
+
+
+def test_voronoi_1d_permutation_equivariant():
+    # the weight belongs to the sample, not to its position: w(xi[pi]) = w(xi)[pi]
+    g = np.random.default_rng(21)
+    xi = g.uniform(-30, 30, 40)
+    w = voronoi_1d(xi, 32.0)
+    for _ in range(5):
+        pi = g.permutation(xi.size)
+        assert np.allclose(voronoi_1d(xi[pi], 32.0), w[pi], rtol=0, atol=1e-13)
+    # each cell is half the gap to each neighbour (interior samples)
+    o = np.argsort(xi)
+    s = xi[o]
+    assert np.allclose(w[o][1:-1], (s[2:] - s[:-2]) / 2.0, rtol=0, atol=1e-13)
+
+
 @pytest.mark.parametrize("p,J,M", [(1, 6, 128), (2, 5, 96), (4, 5, 128)])
 def test_cgls_recovers_and_matches_qr(p, J, M):
     B = Basis1D(p, J)
@@ -279,3 +304,21 @@ def test_cgls_recovers_and_matches_qr(p, J, M):
     x1, _, _ = cgls(op.apply, op.adjoint, y, tol=1e-13, maxit=500)
     x2 = qr_lstsq(op.T, y)
     assert np.max(np.abs(x1 - x2)) / np.max(np.abs(x2)) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["radial_db4_J8", "grid_db4_J9"])
+def test_golden_files_match_their_cases(name):
+    # the stored sampled rows are the oracle's T x of the case's seeded inputs
+    # (guards the golden files against a drift of the input generators)
+    import os
+
+    from oracle.operator import Basis1D, Operator2D
+    from tests.golden.cases import CASES
+
+    c = CASES[name]()
+    gold = np.load(os.path.join(os.path.dirname(__file__), "golden", name + ".npz"))
+    rows = c["rows"][:32]
+    op = Operator2D(Basis1D(c["p"], c["J"]), c["xi"][rows], None if c["mu"] is None else c["mu"][rows])
+    assert np.max(np.abs(op.apply(c["x"]) - gold["T"][:32])) <= 1e-13 * np.max(np.abs(gold["T"]))
+    n = (2 ** c["J"]) ** 2 if c["coefs"] is None else c["coefs"].size
+    assert gold["TH"].shape == (n,) and np.all(np.isfinite(gold["TH"]))
