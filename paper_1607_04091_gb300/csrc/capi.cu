@@ -261,6 +261,15 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
   return GS_OK;
 }
 
+gs_status take_device_timeout(Plan* P) {
+  int v = 0;
+  GS_CUDA(cudaMemcpy(&v, P->flag + FL_TIMEOUT, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v == 0) return GS_OK;
+  GS_CUDA(cudaMemset(P->flag + FL_TIMEOUT, 0, sizeof(int)));
+  set_error("a bounded device wait gave up (a tensor-core kernel of this plan skipped its output)");
+  return GS_ETIMEOUT;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -349,7 +358,13 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
               (long long)plan->P.M, (long long)plan->P.ncoef);
     return GS_EINVAL;
   }
-  return solve(&plan->P, (const double*)y, (double*)x, o, info, (cudaStream_t)stream);
+  gs_status r = solve(&plan->P, (const double*)y, (double*)x, o, info, (cudaStream_t)stream);
+  const gs_status t = take_device_timeout(&plan->P);
+  if (t != GS_OK) {
+    if (info) info->status = t;
+    return t;
+  }
+  return r;
 }
 
 gs_status gs_boundary_constants(int p, double* h, double* UL, double* VL, double* v0L, double* UR, double* VR,
@@ -467,7 +482,15 @@ gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void
     set_error("a plan appears twice in the batch (its workspaces would be shared)");
     return GS_EINVAL;
   }
-  return solve_batch(ps.data(), B, ys.data(), xs.data(), o, infos, (cudaStream_t)stream);
+  gs_status r = solve_batch(ps.data(), B, ys.data(), xs.data(), o, infos, (cudaStream_t)stream);
+  for (int i = 0; i < B; ++i) {
+    const gs_status t = take_device_timeout(ps[i]);
+    if (t != GS_OK) {
+      if (infos) infos[i].status = t;
+      r = t;
+    }
+  }
+  return r;
 }
 
 const char* gs_strerror(gs_status s) {

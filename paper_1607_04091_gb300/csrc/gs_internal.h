@@ -193,6 +193,12 @@ gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaS
 enum { S_GAMMA = 0, S_DELTA, S_ALPHA, S_BETA, S_GNEW, S_THR2, S_S0, S_ITER, S_MAXIT, S_TMP, S_LOOP };
 enum { F_RUN = 0, F_CONV = 1, F_BREAK = 2, F_MAXIT = 3 };
 constexpr int FL_ARRIVE = 4;
+// Plan::flag[FL_TIMEOUT] != 0: a bounded device wait of a kernel gave up (the
+// kernel skipped its output); gs_solve reports it as GS_ETIMEOUT and clears it.
+constexpr int FL_TIMEOUT = 8;
+// GS_OK, or GS_ETIMEOUT (flag cleared) when a kernel of the plan recorded a
+// timed-out wait; synchronises with the device
+gs_status take_device_timeout(Plan* P);
 
 // The vector update of a CG step fused into the adjoint's last pass (2D plans):
 // after z = T^H q, x += alpha p and s -= alpha z over all coefficients, with the

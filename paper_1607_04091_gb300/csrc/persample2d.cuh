@@ -467,57 +467,10 @@ __global__ void __launch_bounds__(256) k_spread2d(
   }
 }
 
-// ---------------------------------------------------------------- tensor-core spread
-// float32, W = 8 taps, 2b = 8 boundary columns, 16 x 16 tiles.  For one work item
-// every output of the spread is a sum over its samples of outer products:
-//   P[x][y]   += (v_s wx_s[x - px_s]) wy_s[y - py_s]      interior, v = u conj(wx wy)
-//   S0[k][y]  += v0_s[k] wy_s[y - py_s]                    x-sides,  v0 = u conj(bx_k) conj(wy)
-//   S1[k][x]  += v1_s[k] wx_s[x - px_s]                    y-sides,  v1 = u conj(wx) conj(by_k)
-//   Cc[kx][ky]+= A_s[kx] conj(by_s[ky])                     corners,  A = u conj(bx)
-// i.e. GEMMs with K = samples.  The samples go in batches of 32:
-//   staging  cp.async copies the next batch's per-sample inputs (taps,
-//            boundary factors, phases, u, grid indices) to the other of two
-//            shared-memory buffers while this batch is built and multiplied;
-//   phase 1  warp q writes operand q (v wx re, v wx im, wx, wy as rows of 32
-//            grid offsets, zero outside the sample's 8 taps) and two boundary
-//            operands, one lane per sample;
-//   phase 2  mma.sync m16n8k8 TF32 with the 3xTF32 split (a_hi b_hi + a_hi b_lo +
-//            a_lo b_hi, float32-level accuracy): warps 0-1 one 16-row block of
-//            the interior each (real and imaginary part share the wy fragments),
-//            warp 2 the x-sides and warp 3 the y-sides, both taken transposed
-//            (rows = grid offset, columns = k), and one half each of the corners.
-// Output: the same partial-tile layout as k_spread2d, written through shared
-// memory with 16-byte stores.
+// ---------------------------------------------------------------- warp-level tensor-core helpers
+// (mma.sync TF32 with the 3xTF32 split and cp.async staging; used by the
+// tensor-core interpolation below)
 namespace tc {
-constexpr int SBT = 32;  // samples per batch (the K of one round)
-constexpr int W = 8, B2 = 8, TILE = 16, PW = TILE + W;
-constexpr int LDO = 24;  // rows of the window operands: 24 grid offsets (conflict-free fragments);
-                         // the second 16-row block reads 8 entries past a row (the next row's),
-                         // which only reach output rows >= 24, never stored
-constexpr int LDT = 36;  // boundary operands stored transposed, [k][sample]: conflict-free
-                         // writes (one lane per sample) and fragment loads
-constexpr int LDS = 16;  // staged rows of 16 floats, 16-byte chunks swizzled (see srow)
-// operand area (floats)
-constexpr int O_AR = 0, O_AI = O_AR + SBT * LDO, O_BX = O_AI + SBT * LDO, O_BY = O_BX + SBT * LDO;
-constexpr int O_V0R = O_BY + SBT * LDO, O_V0I = O_V0R + B2 * LDT, O_V1R = O_V0I + B2 * LDT;
-constexpr int O_V1I = O_V1R + B2 * LDT, O_CR = O_V1I + B2 * LDT, O_CI = O_CR + B2 * LDT;
-constexpr int O_K = O_CI + B2 * LDT;  // [Re A_0..7 | Im A_0..7][sample]
-constexpr int N_OPER = O_K + 2 * B2 * LDT;
-// staging, two buffers after the operands (offsets within a buffer, floats)
-constexpr int S_WIN = 0, S_BX = S_WIN + SBT * LDS, S_BY = S_BX + SBT * LDS;
-constexpr int S_W = S_BY + SBT * LDS;  // [j][4]: wx re, im, wy re, im
-constexpr int S_U = S_W + 4 * SBT;     // [j][2]
-constexpr int S_FL = S_U + 2 * SBT;    // [j][2] int
-constexpr int S_SIZE = S_FL + 2 * SBT;
-constexpr int S_STAGE = N_OPER;
-constexpr int N_SMEM = S_STAGE + 2 * S_SIZE;
-static_assert(S_STAGE % 4 == 0 && S_SIZE % 4 == 0, "16-byte staging");
-// partial tile (float2) and corner exchange, reusing the operand area at the end
-constexpr int PART = PW * PW + 2 * B2 * PW + B2 * B2;
-constexpr int O_CS = 2 * PART;  // [2 warps][16][8] floats
-static_assert(O_CS + 2 * 16 * 8 <= N_OPER, "epilogue must fit the operand area");
-static_assert(PART % 2 == 0, "partial tile copied as float4");
-
 // x = hi + lo with hi = x rounded to the 10 explicit mantissa bits of TF32 (add half
 // an ulp of TF32 to the bit pattern, then clear the 13 low bits: round to nearest,
 // ties away from zero) and lo = x - hi exact in float32, |lo| <= 2^-11 |x|.  lo goes
@@ -534,33 +487,7 @@ __device__ inline void mma(float* c, const uint32_t* a, const uint32_t* b) {
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-// A fragment (16 x 8, rows m0.., k-columns k0..) from an operand stored [k][m]
-__device__ inline void load_a(const float* A, int ld, int m0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
-  const int g = lane >> 2, t = lane & 3;
-  split(A[(k0 + t) * ld + m0 + g], hi[0], lo[0]);
-  split(A[(k0 + t) * ld + m0 + g + 8], hi[1], lo[1]);
-  split(A[(k0 + t + 4) * ld + m0 + g], hi[2], lo[2]);
-  split(A[(k0 + t + 4) * ld + m0 + g + 8], hi[3], lo[3]);
-}
-// B fragment (8 x 8, k-rows k0.., columns n0..) from an operand stored [k][n]
-__device__ inline void load_b(const float* B, int ld, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
-  const int g = lane >> 2, t = lane & 3;
-  split(B[(k0 + t) * ld + n0 + g], hi[0], lo[0]);
-  split(B[(k0 + t + 4) * ld + n0 + g], hi[1], lo[1]);
-}
-// A fragment from an operand stored [m][k]
-__device__ inline void load_aT(const float* A, int ld, int m0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
-  const int g = lane >> 2, t = lane & 3;
-  split(A[(m0 + g) * ld + k0 + t], hi[0], lo[0]);
-  split(A[(m0 + g + 8) * ld + k0 + t], hi[1], lo[1]);
-  split(A[(m0 + g) * ld + k0 + t + 4], hi[2], lo[2]);
-  split(A[(m0 + g + 8) * ld + k0 + t + 4], hi[3], lo[3]);
-}
-// float offset of 16-byte chunk c (0..3) of staged row j: chunks XOR-swizzled by
-// (j >> 1) & 3, so that eight consecutive rows reading (or writing) the same chunk
-// hit eight distinct 4-bank groups
-__device__ inline int srow(int j, int c) { return j * LDS + 4 * (c ^ ((j >> 1) & 3)); }
-// B fragment from an operand stored [n][k]
+// B fragment (8 x 8, k-rows k0.., columns n0..) from an operand stored [n][k]
 __device__ inline void load_bT(const float* B, int ld, int n0, int k0, int lane, uint32_t* hi, uint32_t* lo) {
   const int g = lane >> 2, t = lane & 3;
   split(B[(n0 + g) * ld + k0 + t], hi[0], lo[0]);
@@ -580,221 +507,13 @@ __device__ inline void cp_async4(void* dst, const void* src) {
 }
 __device__ inline void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ inline void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Copies the inputs of samples sb .. sb+nb-1 to the staging area: warp 0 the 16
-// taps (4 x 16 B), warp 1 the 8 x-boundary factors, warp 2 the 8 y-boundary
-// factors (4 x 16 B each), warp 3 the two phases, u and the two grid indices.
-__device__ inline void stage(float* sm, int wid, int lane, int sb, int nb, const float* __restrict__ win,
-                             const float2* __restrict__ w, const float2* __restrict__ bf,
-                             const float2* __restrict__ u, const int32_t* __restrict__ perm,
-                             const int32_t* __restrict__ fl, int64_t M) {
-  if (lane >= nb) return;
-  const int64_t s = sb + lane;
-  if (wid == 0) {
-    const float* src = win + s * (2 * W);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) cp_async16(sm + S_WIN + srow(lane, c), src + 4 * c);
-  } else if (wid < 3) {
-    const float2* src = bf + (s + (wid == 2 ? M : 0)) * B2;
-    float* dst = sm + (wid == 1 ? S_BX : S_BY);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) cp_async16(dst + srow(lane, c), src + 2 * c);
-  } else {
-    cp_async8(sm + S_W + 4 * lane, w + s);
-    cp_async8(sm + S_W + 4 * lane + 2, w + M + s);
-    cp_async8(sm + S_U + 2 * lane, u + (perm ? perm[s] : s));
-    cp_async4(sm + S_FL + 2 * lane, fl + s);
-    cp_async4(sm + S_FL + 2 * lane + 1, fl + M + s);
-  }
-}
 }  // namespace tc
 
-static __global__ void __launch_bounds__(128, 5) k_spread2d_tc(
-    const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl, const float* __restrict__ win,
-    const float2* __restrict__ w, const float2* __restrict__ bf, const float2* __restrict__ u,
-    const int32_t* __restrict__ perm, int64_t M, int nbx, float2* __restrict__ part, int64_t stride) {
-  using namespace tc;
-  extern __shared__ __align__(16) float sm[];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int it = order[blockIdx.x];  // work item (larger items launch first)
-  const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
-  const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
-  stage(sm + S_STAGE, wid, lane, s0, min(SBT, s1 - s0), win, w, bf, u, perm, fl, M);
-  cp_commit();
-  for (int i = threadIdx.x; i < N_OPER; i += blockDim.x) sm[i] = 0.0f;
-  // accumulators.  Warps 0-1: interior rows m0..m0+15, [re: 0-2 | im: 3-5][n-block].
-  // Warps 2-3: side product (2 = x-sides S0, 3 = y-sides S1) [2 m-blocks][re | im] in
-  // 0-3 and half of the corner product in 4.
-  float acc[6][4];
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0f;
-  const int m0 = (wid & 1) * 16;
-  const float* Aside = sm + (wid == 2 ? O_BY : O_BX);  // side A (transposed): wy for S0, wx for S1
-  const float* Bs0 = sm + (wid == 2 ? O_V0R : O_V1R);
-  const float* Bs1 = sm + (wid == 2 ? O_V0I : O_V1I);
-  const float* Bc = sm + (wid == 2 ? O_CR : O_CI);
-  // phase-1 role: the 32-wide operand this warp owns and where its last window sat
-  float* Own = sm + (wid == 0 ? O_AR : wid == 1 ? O_AI : wid == 2 ? O_BX : O_BY);
-  int prev = -1;
-  int buf = 0;
-  for (int sb = s0; sb < s1; sb += SBT, buf ^= 1) {
-    const int nb = min(SBT, s1 - sb);
-    cp_wait_all();
-    __syncthreads();  // staging of this batch visible; phase 2 of the last batch done
-    // the next batch's inputs go to the other buffer (last read by the previous phase 1)
-    if (sb + SBT < s1)
-      stage(sm + S_STAGE + (buf ^ 1) * S_SIZE, wid, lane, sb + SBT, min(SBT, s1 - sb - SBT), win, w, bf, u, perm,
-            fl, M);
-    cp_commit();
-    const float* st = sm + S_STAGE + buf * S_SIZE;
-    {
-      const int j = lane;
-      float* row = Own + j * LDO;
-      if (prev >= 0) {
-#pragma unroll
-        for (int a = 0; a < W; ++a) row[prev + a] = 0.0f;
-        prev = -1;
-      }
-      if (j < nb) {
-        const float4 ww = *reinterpret_cast<const float4*>(st + S_W + 4 * j);
-        const float2 wxs = make_float2(ww.x, ww.y), wys = make_float2(ww.z, ww.w);
-        const float2 us = *reinterpret_cast<const float2*>(st + S_U + 2 * j);
-        const int* flj = reinterpret_cast<const int*>(st + S_FL + 2 * j);
-        const int pos = (wid == 3) ? flj[1] - oy + 1 : flj[0] - ox + 1;
-        const int cb = (wid == 3) ? 2 : 0;  // chunks of the y taps (8..15) or x taps (0..7)
-        const float4 t0 = *reinterpret_cast<const float4*>(st + S_WIN + srow(j, cb));
-        const float4 t1 = *reinterpret_cast<const float4*>(st + S_WIN + srow(j, cb + 1));
-        const float tap[W] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-        float scale = 1.0f;
-        if (wid < 2) {
-          const float2 vi = cmulc(cmulc(us, wxs), wys);
-          scale = (wid == 0) ? vi.x : vi.y;
-        }
-#pragma unroll
-        for (int a = 0; a < W; ++a) row[pos + a] = scale * tap[a];
-        prev = pos;
-        // boundary operands: warp 0 V0 (x-sides), 1 V1 (y-sides), 2 A = u conj(bx), 3 conj(by)
-        const float* bp = st + ((wid == 0 || wid == 2) ? S_BX : S_BY);
-        const float2 uwx = cmulc(us, wxs), uwy = cmulc(us, wys);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const float4 f = *reinterpret_cast<const float4*>(bp + srow(j, h));
-          const float2 bk[2] = {make_float2(f.x, f.y), make_float2(f.z, f.w)};
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int k = 2 * h + e;
-            if (wid == 0) {
-              const float2 v0 = cmulc(uwy, bk[e]);
-              sm[O_V0R + k * LDT + j] = v0.x;
-              sm[O_V0I + k * LDT + j] = v0.y;
-            } else if (wid == 1) {
-              const float2 v1 = cmulc(uwx, bk[e]);
-              sm[O_V1R + k * LDT + j] = v1.x;
-              sm[O_V1I + k * LDT + j] = v1.y;
-            } else if (wid == 2) {
-              const float2 ak = cmulc(us, bk[e]);
-              sm[O_K + k * LDT + j] = ak.x;
-              sm[O_K + (B2 + k) * LDT + j] = ak.y;
-            } else {
-              sm[O_CR + k * LDT + j] = bk[e].x;
-              sm[O_CI + k * LDT + j] = -bk[e].y;
-            }
-          }
-        }
-      } else {  // empty slot: its boundary rows are zero
-#pragma unroll
-        for (int k = 0; k < B2; ++k) {
-          if (wid == 0) sm[O_V0R + k * LDT + j] = sm[O_V0I + k * LDT + j] = 0.0f;
-          else if (wid == 1) sm[O_V1R + k * LDT + j] = sm[O_V1I + k * LDT + j] = 0.0f;
-          else if (wid == 2) sm[O_K + k * LDT + j] = sm[O_K + (B2 + k) * LDT + j] = 0.0f;
-          else sm[O_CR + k * LDT + j] = sm[O_CI + k * LDT + j] = 0.0f;
-        }
-      }
-    }
-    __syncthreads();  // operands complete
-    // The three products of the split go term by term over the warp's tiles, so
-    // that consecutive MMAs never update the same accumulator.
-    if (wid < 2) {
-#pragma unroll
-      for (int k0 = 0; k0 < SBT; k0 += 8) {
-        uint32_t ah[2][4], al[2][4], bh[3][2], bl[3][2];
-        load_a(sm + O_AR, LDO, m0, k0, lane, ah[0], al[0]);
-        load_a(sm + O_AI, LDO, m0, k0, lane, ah[1], al[1]);
-#pragma unroll
-        for (int nbk = 0; nbk < 3; ++nbk) load_b(sm + O_BY, LDO, nbk * 8, k0, lane, bh[nbk], bl[nbk]);
-#pragma unroll
-        for (int term = 0; term < 3; ++term)
-#pragma unroll
-          for (int nbk = 0; nbk < 3; ++nbk)
-#pragma unroll
-            for (int ri = 0; ri < 2; ++ri)
-              mma(acc[3 * ri + nbk], term == 2 ? al[ri] : ah[ri], term == 1 ? bl[nbk] : bh[nbk]);
-      }
-    } else {
-#pragma unroll
-      for (int k0 = 0; k0 < SBT; k0 += 8) {
-        // tiles: 0-3 side [m-block][re | im], 4 corner
-        uint32_t ah[3][4], al[3][4], bh[3][2], bl[3][2];
-        load_a(Aside, LDO, 0, k0, lane, ah[0], al[0]);
-        load_a(Aside, LDO, 16, k0, lane, ah[1], al[1]);
-        load_aT(sm + O_K, LDT, 0, k0, lane, ah[2], al[2]);
-        load_bT(Bs0, LDT, 0, k0, lane, bh[0], bl[0]);
-        load_bT(Bs1, LDT, 0, k0, lane, bh[1], bl[1]);
-        load_bT(Bc, LDT, 0, k0, lane, bh[2], bl[2]);
-#pragma unroll
-        for (int term = 0; term < 3; ++term) {
-#pragma unroll
-          for (int tl = 0; tl < 4; ++tl)
-            mma(acc[tl], term == 2 ? al[tl >> 1] : ah[tl >> 1], term == 1 ? bl[tl & 1] : bh[tl & 1]);
-          mma(acc[4], term == 2 ? al[2] : ah[2], term == 1 ? bl[2] : bh[2]);
-        }
-      }
-    }
-  }
-  cp_wait_all();
-  __syncthreads();  // operands no longer read: the area holds the partial tile now
-  float* T = sm;    // float2 [PART] as floats
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = g + ((q & 2) ? 8 : 0), c = 2 * t + (q & 1);
-    if (wid < 2) {  // interior: rows x, columns y
-#pragma unroll
-      for (int nbk = 0; nbk < 3; ++nbk)
-        if (m0 + r < PW) {
-          const int o = (m0 + r) * PW + nbk * 8 + c;
-          T[2 * o] = acc[nbk][q];
-          T[2 * o + 1] = acc[3 + nbk][q];
-        }
-    } else {  // sides: rows are the grid offset (y for S0, x for S1), columns k
-#pragma unroll
-      for (int mb = 0; mb < 2; ++mb)
-        if (16 * mb + r < PW) {
-          const int o = PW * PW + (wid == 3 ? B2 * PW : 0) + c * PW + 16 * mb + r;
-          T[2 * o] = acc[2 * mb][q];
-          T[2 * o + 1] = acc[2 * mb + 1][q];
-        }
-      sm[O_CS + ((wid - 2) * 16 + r) * 8 + c] = acc[4][q];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < B2 * B2) {
-    const int kx = threadIdx.x % B2, ky = threadIdx.x / B2;
-    const float rr = sm[O_CS + (0 * 16 + kx) * 8 + ky];       // Re(A) Re(conj by)
-    const float ir = sm[O_CS + (0 * 16 + 8 + kx) * 8 + ky];   // Im(A) Re(conj by)
-    const float ri = sm[O_CS + (1 * 16 + kx) * 8 + ky];       // Re(A) Im(conj by)
-    const float ii = sm[O_CS + (1 * 16 + 8 + kx) * 8 + ky];   // Im(A) Im(conj by)
-    const int o = PW * PW + 2 * B2 * PW + kx + B2 * ky;
-    T[2 * o] = rr - ii;
-    T[2 * o + 1] = ri + ir;
-  }
-  __syncthreads();
-  float4* out = reinterpret_cast<float4*>(part + it * stride);
-  const float4* src = reinterpret_cast<const float4*>(T);
-  for (int i = threadIdx.x; i < PART / 2; i += blockDim.x) out[i] = src[i];
-}
+}  // namespace dev
+}  // namespace gs
+#include "spread2d_tcgen05.cuh"
+namespace gs {
+namespace dev {
 
 // ---------------------------------------------------------------- tensor-core interpolation
 // float32, W = 8 taps, 2b = 8 boundary columns, 16 x 16 tiles.  With the staged
@@ -1194,14 +913,15 @@ template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st) {
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
-  if (sizeof(R) == 4 && D.m == 4 && b2 == 8 && tile == 16 && D.part_stride == tc::PART && !std::getenv("GS_NO_TC")) {
-    const size_t sh = (size_t)tc::N_SMEM * sizeof(float);
-    gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc, sh);
+  if (sizeof(R) == 4 && D.m == 4 && b2 == 8 && tile == 16 && D.part_stride == tc5::PART && !std::getenv("GS_NO_TC")) {
+    const size_t sh = (size_t)tc5::N_SMEM * sizeof(float);
+    gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc5, sh);
     if (e != GS_OK) return e;
     GS_LAUNCH("spread2d<f32>", st,
-              k_spread2d_tc<<<P->nwork, 128, sh, st>>>(P->work, P->work_order, P->fl, (const float*)D.win, (const float2*)D.w,
-                                                       (const float2*)D.bf, (const float2*)u, perm, P->M, P->nbx,
-                                                       (float2*)part, D.part_stride));
+              k_spread2d_tc5<<<P->nwork, tc5::THREADS, sh, st>>>(P->work, P->work_order, P->fl, (const float*)D.win,
+                                                        (const float2*)D.w, (const float2*)D.bf, (const float2*)u, perm,
+                                                        P->M, P->nbx, (float2*)part, D.part_stride,
+                                                        P->flag + FL_TIMEOUT));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   }

@@ -566,6 +566,7 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
   GS_TRY(set_work(P, P->chunk > 0 ? P->chunk : (dims == 1 ? CHUNK1 : CHUNK2), st));
   GS_TRY(dalloc(&P->scal, 64));
   GS_TRY(dalloc(&P->flag, 16));
+  GS_CUDA(cudaMemsetAsync(P->flag, 0, 16 * sizeof(int), st));
   GS_TRY(dalloc(&P->y64, (size_t)2 * M));
   GS_TRY(dalloc(&P->r64, (size_t)2 * M));
   GS_TRY(dalloc(&P->x64, (size_t)2 * P->ncoef));
