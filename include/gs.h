@@ -175,14 +175,17 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
                    gs_solve_info* info, void* stream);
 
 /* B independent least-squares solves (one plan each, plans distinct) with the
- * options of gs_solve.  Each GS_SOLVE_MIXED solve with tol >= 1e-7 runs as one
- * CUDA graph (nested while-conditional nodes: refinement
- * passes around CG iterations, float64 residual and stop test on the device);
- * the B graphs are launched round-robin on 16 library-owned streams ordered
- * after `stream`, with no host synchronisation until all have finished.  Other
- * option combinations fall back to gs_solve per problem.  y[i], x[i] as in
- * gs_solve; infos (host, B entries) may be NULL.  Returns the first non-OK
- * status of any problem (GS_ENOTCONV included). */
+ * options of gs_solve.  With GS_SOLVE_MIXED and tol >= 1e-7 the whole batch runs
+ * as ONE CUDA graph launched on `stream`: 16 independent chains of whole solves
+ * (each solve with its nested while-conditional nodes: refinement passes around
+ * CG iterations, float64 residual and stop test on the device), problems assigned
+ * to chains longest-first by estimated cost (CG iterations of the plan's previous
+ * solve times a per-iteration time model), no host involvement until the graph has
+ * finished.  The instantiated graph is cached while the same plans, buffers and
+ * options recur (rebuilt once when measured iteration counts first become
+ * available).  Other options run gs_solve per problem on 16 library-owned streams.
+ * y[i], x[i] as in gs_solve; infos (host, B entries) may be NULL.  Returns the
+ * first non-OK status of any problem (GS_ENOTCONV included). */
 gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
                          const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
 
@@ -208,6 +211,15 @@ gs_status gs_cnn_gradients(gs_cnn net, const float* u, const float* target, int 
 /* all weights then all biases, layer by layer ([c_out][c_in][3][3], [c_out]); *count always set */
 gs_status gs_cnn_weights(gs_cnn net, float* host, int64_t* count);
 gs_status gs_cnn_set_weights(gs_cnn net, const float* host, int64_t count);
+
+/* Batched least squares from learned starts: for each problem the start of
+ * gs_solve_learned (x0 = rms(u) net(u / rms(u)), u = T^H y[i]), then gs_solve_batch
+ * with x0_given = 1 (each start kept only if ||T^H (y - T x0)|| < ||T^H y||, else
+ * that problem starts from zero).  All plans 2D with the network's N x N grid; other
+ * arguments as gs_solve_batch.  The paper has no counterpart (an addition beside the
+ * method). */
+gs_status gs_solve_batch_learned(const gs_plan* plans, int B, gs_cnn net, const void* const* y, void* const* x,
+                                 const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
 
 /* A training pair for the network: u_img = image of u / rms(u), u = T^H y
  * (float32 adjoint), and, when x and x_img are non-NULL, x_img = image of

@@ -41,7 +41,7 @@ class GsError(RuntimeError):
 _lib = None
 EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_apply_T", "gs_apply_TH",
            "gs_apply_TH_noalloc", "gs_solve_batch", "gs_cnn_create", "gs_cnn_destroy", "gs_cnn_forward",
-           "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned", "gs_cnn_pair",
+           "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned", "gs_solve_batch_learned", "gs_cnn_pair",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
            "gs_last_error_detail"]
 
@@ -88,9 +88,12 @@ def load(path: str = LIB):
     lib.gs_cnn_set_weights.argtypes = [vp, fp, i64]
     lib.gs_solve_learned.argtypes = [vp, vp, vp, vp, ctypes.POINTER(GsSolveOpts), ctypes.POINTER(GsSolveInfo),
                                      ctypes.POINTER(ctypes.c_int), vp]
+    lib.gs_solve_batch_learned.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp),
+                                           ctypes.POINTER(vp), ctypes.POINTER(GsSolveOpts),
+                                           ctypes.POINTER(GsSolveInfo), vp]
     lib.gs_cnn_pair.argtypes = [vp, vp, vp, vp, vp, vp]
     for f in ["gs_cnn_create", "gs_cnn_forward", "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights",
-              "gs_cnn_set_weights", "gs_solve_learned", "gs_cnn_pair"]:
+              "gs_cnn_set_weights", "gs_solve_learned", "gs_solve_batch_learned", "gs_cnn_pair"]:
         getattr(lib, f).restype = ctypes.c_int
     lib.gs_strerror.argtypes = [ctypes.c_int]
     lib.gs_strerror.restype = ctypes.c_char_p
@@ -391,6 +394,27 @@ def gs_solve_learned(plan, net, y, x, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED,
         _check(st, "gs_solve_learned")
     return ({"iterations": info.iterations, "outer": info.outer, "rel_normres": info.rel_normres,
              "rel_res": info.rel_res, "status": info.status}, bool(used.value))
+
+
+def gs_solve_batch_learned(plans, net, ys, xs, tol=1e-6, maxit=1000, mode=GS_SOLVE_MIXED, max_outer=8,
+                           inner_rtol=0.0, stream=None):
+    """gs_solve_batch from the learned start of each problem; list of info dicts."""
+    import torch
+    B = len(plans)
+    hs = (ctypes.c_void_p * B)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    for p, y, x in zip(plans, ys, xs):
+        _, M, _, nc = gs_plan_sizes(p)
+        _dev(y, torch.complex128, M)
+        _dev(x, torch.complex128, nc)
+    yp = (ctypes.c_void_p * B)(*[y.data_ptr() for y in ys])
+    xp = (ctypes.c_void_p * B)(*[x.data_ptr() for x in xs])
+    o = GsSolveOpts(tol, maxit, mode, 1, max_outer, inner_rtol)
+    infos = (GsSolveInfo * B)()
+    st = load().gs_solve_batch_learned(hs, B, net.handle, yp, xp, ctypes.byref(o), infos, _stream(stream))
+    if st not in (GS_OK, GS_ENOTCONV):
+        _check(st, "gs_solve_batch_learned")
+    return [{"iterations": i.iterations, "outer": i.outer, "rel_normres": i.rel_normres, "rel_res": i.rel_res,
+             "status": i.status} for i in infos]
 
 
 def gs_cnn_pair(plan, y, x=None, stream=None):

@@ -12,6 +12,8 @@
 
 #include <cstring>
 
+#include <atomic>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -243,6 +245,8 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
     delete h;
     return GS_EUNSUPPORTED;
   }
+  static std::atomic<uint64_t> next_uid{1};
+  P->uid = next_uid.fetch_add(1);
   GS_CUDA(cudaGetDevice(&P->dev));
   GS_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   for (int i = 0; i < 3; ++i) {

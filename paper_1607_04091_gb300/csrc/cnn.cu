@@ -557,20 +557,21 @@ __global__ void k_c128_to_c64(const double2* __restrict__ a, float2* __restrict_
 }  // namespace
 }  // namespace gs
 
-extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, void* x, const gs_solve_opts* opts,
-                                      gs_solve_info* info, int* used_warm_start, void* stream) {
+namespace gs {
+namespace {
+// x = rms(u) * net(u / rms(u)), u = T^H y (float32 adjoint): the learned start
+gs_status learned_start(gs_plan plan, gs_cnn net, const void* y, void* x, cudaStream_t st) {
   if (!plan || !net || !y || !x) {
-    set_error("gs_solve_learned: plan, net, y and x must be non-NULL");
+    set_error("learned start: plan, net, y and x must be non-NULL");
     return GS_EINVAL;
   }
   Plan* P = &plan->P;
   gs_cnn_s* N = net;
   if (P->dims != 2 || N->H != P->N || N->W != P->N) {
-    set_error("gs_solve_learned: the network's image (%d x %d) must be the plan's 2D coefficient grid (%lld)", N->H,
+    set_error("learned start: the network's image (%d x %d) must be the plan's 2D coefficient grid (%lld)", N->H,
               N->W, (long long)P->N);
     return GS_EINVAL;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   const int64_t nc = P->ncoef, M = P->M;
   PrecData<float>& F = P->f;
   // u = T^H y (float32), its image scaled to unit rms
@@ -587,6 +588,15 @@ extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, v
   GS_TRY(gs_cnn_forward(N, img_in, img_out, 1, 1, st));
   k_image_to_coef<<<blocks(nc), 256, 0, st>>>(img_out, nc, scale, (double2*)x);
   GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, void* x, const gs_solve_opts* opts,
+                                      gs_solve_info* info, int* used_warm_start, void* stream) {
+  GS_TRY(learned_start(plan, net, y, x, (cudaStream_t)stream));
+  Plan* P = &plan->P;
   // solve from x0; the solve keeps x0 only if ||T^H (y - T x0)|| < ||T^H y|| (else zero start)
   gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
   if (opts) o = *opts;
@@ -598,6 +608,20 @@ extern "C" gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, v
     *used_warm_start = (w != 0.0) ? 1 : 0;
   }
   return r;
+}
+
+extern "C" gs_status gs_solve_batch_learned(const gs_plan* plans, int B, gs_cnn net, const void* const* y,
+                                            void* const* x, const gs_solve_opts* opts, gs_solve_info* infos,
+                                            void* stream) {
+  if (!plans || !y || !x || B < 1 || !net) {
+    set_error("gs_solve_batch_learned: need plans, net, y, x non-NULL and B >= 1");
+    return GS_EINVAL;
+  }
+  for (int i = 0; i < B; ++i) GS_TRY(learned_start(plans[i], net, y[i], x[i], (cudaStream_t)stream));
+  gs_solve_opts o = {1e-6, 1000, GS_SOLVE_MIXED, 0, 8, 0.0};
+  if (opts) o = *opts;
+  o.x0_given = 1;
+  return gs_solve_batch(plans, B, y, x, &o, infos, stream);
 }
 
 extern "C" gs_status gs_cnn_pair(gs_plan plan, const void* y, const void* x, float* u_img, float* x_img,

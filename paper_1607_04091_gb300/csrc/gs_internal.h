@@ -150,6 +150,9 @@ struct Plan {
   cudaEvent_t ev_fork[3] = {nullptr, nullptr, nullptr}, ev_join[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};  // whole mixed solve as one graph [zero, given start]
   bool solve_graph_failed = false;
+  bool solve_kernels_warm = false;  // the solve's kernels ran once outside any capture
+  uint64_t uid = 0;                 // unique per plan in the process (batch-graph cache key)
+  int last_iters = 0;               // CG iterations of the last graph solve (batch schedule cost)
 };
 
 // Work launched on side_stream(P, st, i) between fork_aux(P, st, i) and

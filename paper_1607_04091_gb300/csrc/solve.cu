@@ -17,6 +17,8 @@
 #include <thread>
 #include <vector>
 
+#include <cstring>
+
 #include "gs_internal.h"
 
 namespace gs {
@@ -592,28 +594,30 @@ __global__ void k_fallback_scalars(double* scal) {
   scal[G_NS2] = scal[S_TMP];
 }
 
-gs_status build_solve_graph(Plan* P, bool with_x0, cudaStream_t st, cudaGraphExec_t* out) {
+// eager applies on the plan's capture stream, so that kernel attributes (dynamic
+// shared memory sizes) are set outside any capture
+gs_status warm_solve_kernels(Plan* P, cudaStream_t st) {
   cudaStream_t cs = P->cap_stream;
   PrecData<float>& F = P->f;
-  const int64_t nc = P->ncoef, M = P->M;
-  // eager applies so that kernel attributes are set outside capture
   GS_CUDA(cudaStreamSynchronize(st));
   GS_TRY(apply_T<float>(P, F, F.vp, F.vq, nullptr, cs));
   GS_TRY(apply_TH<float>(P, F, F.vq, F.vz, nullptr, cs));
   GS_TRY(apply_T<double>(P, P->d, (const double2*)P->x64, P->d.vq, nullptr, cs));
   GS_CUDA(cudaStreamSynchronize(cs));
-  cudaGraph_t G = nullptr;
-  GS_CUDA(cudaGraphCreate(&G, 0));
-  struct Guard {
-    cudaGraph_t g;
-    ~Guard() {
-      if (g) cudaGraphDestroy(g);
-    }
-  } guard{G};
+  return GS_OK;
+}
+
+// Adds the nodes of one whole mixed solve of plan P (data in P->y64, start in
+// P->x64 when with_x0, parameters in P->scal) to graph G after node dep (NULL:
+// no dependency); *last receives its final node.
+gs_status add_solve_nodes(Plan* P, bool with_x0, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNode_t* last) {
+  cudaStream_t cs = P->cap_stream;
+  PrecData<float>& F = P->f;
+  const int64_t nc = P->ncoef, M = P->M;
   cudaGraphConditionalHandle ho, hi;
   GS_CUDA(cudaGraphConditionalHandleCreate(&ho, G, 0, cudaGraphCondAssignDefault));
   cudaGraphNode_t n_setup, n_oenter, n_outer, n_final;
-  GS_TRY(add_child(G, nullptr, cs, [&](cudaStream_t c) -> gs_status {
+  GS_TRY(add_child(G, dep ? &dep : nullptr, cs, [&](cudaStream_t c) -> gs_status {
     GS_TRY(norm2_into<double>(P, (const double2*)P->y64, M, G_HY2, nullptr, c));
     if (!with_x0) GS_CUDA(cudaMemsetAsync(P->x64, 0, nc * sizeof(double2), c));
     k_copy<double><<<grid_for(M), 256, 0, c>>>((double2*)P->r64, (const double2*)P->y64, M);
@@ -667,6 +671,23 @@ gs_status build_solve_graph(Plan* P, bool with_x0, cudaStream_t st, cudaGraphExe
   GS_TRY(add_child(G, &n_outer, cs, [&](cudaStream_t c) -> gs_status {
     return norm2_into<double>(P, (const double2*)P->r64, M, G_NR2, nullptr, c);
   }, &n_final));
+  *last = n_final;
+  return GS_OK;
+}
+
+gs_status build_solve_graph(Plan* P, bool with_x0, cudaStream_t st, cudaGraphExec_t* out) {
+  GS_TRY(warm_solve_kernels(P, st));
+  P->solve_kernels_warm = true;
+  cudaGraph_t G = nullptr;
+  GS_CUDA(cudaGraphCreate(&G, 0));
+  struct Guard {
+    cudaGraph_t g;
+    ~Guard() {
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{G};
+  cudaGraphNode_t last = nullptr;
+  GS_TRY(add_solve_nodes(P, with_x0, G, nullptr, &last));
   GS_CUDA(cudaGraphInstantiate(out, G, 0));
   return GS_OK;
 }
@@ -701,6 +722,7 @@ gs_status graph_solve_info(Plan* P, const gs_solve_opts& o, gs_solve_info* info)
   const double hb2 = sc[G_HB2], hy2 = sc[G_HY2];
   inf.iterations = (int)sc[G_TOTAL];
   inf.outer = (int)sc[G_OUTER];
+  P->last_iters = inf.iterations;
   inf.rel_normres = hb2 > 0 ? std::sqrt(sc[G_NS2] / hb2) : 0.0;
   inf.rel_res = hy2 > 0 ? std::sqrt((hb2 > 0 ? sc[G_NR2] : hy2) / hy2) : 0.0;
   gs_status rc = GS_OK;
@@ -875,8 +897,140 @@ gs_status get_pool(StreamPool** out) {
 }
 }  // namespace
 
+// ---------------------------------------------------------------- one graph per batch
+// A batch of mixed solves runs as ONE CUDA graph: LANES dependency chains, each a
+// sequence of whole solves (data gather and parameters, the solve's nodes with
+// its nested while loops, the copy of the result), the chains independent of one
+// another.  Problems go to chains by longest-processing-time-first: sorted by
+// estimated cost, each to the chain with the least work so far.  The cost of a
+// solve is its CG iterations times a per-iteration time model (a fixed ~40 us of
+// small kernels plus terms in M and the coefficient count); the iterations are
+// those of the plan's previous solve when every plan has one (the schedule then
+// tunes itself on measured counts), else a common guess.  The instantiated graph
+// is cached per device, keyed by the plans, buffers and options, and rebuilt once
+// when measured iteration counts first become available.
+constexpr int LANES = 16;
+struct BatchGraph {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  bool measured = false;
+};
+BatchGraph g_batch[64];
+
+double solve_cost(const Plan* P, bool measured) {
+  const double per_it = 40.0 + (double)P->M / 3000.0 + (double)P->ncoef / 1000.0;  // us
+  return (measured ? (double)P->last_iters + 1.0 : 100.0) * per_it;
+}
+
+gs_status build_batch_graph(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
+                            bool measured, cudaStream_t st, cudaGraphExec_t* out) {
+  for (int p = 0; p < B; ++p)
+    if (!plans[p]->solve_kernels_warm) {
+      GS_TRY(warm_solve_kernels(plans[p], st));
+      plans[p]->solve_kernels_warm = true;
+    }
+  std::vector<int> ord(B);
+  std::vector<double> cost(B);
+  for (int p = 0; p < B; ++p) {
+    ord[p] = p;
+    cost[p] = solve_cost(plans[p], measured);
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<std::vector<int>> lane(LANES);
+  std::vector<double> load(LANES, 0.0);
+  for (int p : ord) {
+    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lane[l].push_back(p);
+    load[l] += cost[p];
+  }
+  cudaGraph_t G = nullptr;
+  GS_CUDA(cudaGraphCreate(&G, 0));
+  struct Guard {
+    cudaGraph_t g;
+    ~Guard() {
+      if (g) cudaGraphDestroy(g);
+    }
+  } guard{G};
+  const double tol2 = o.tol * o.tol, irt2 = o.inner_rtol * o.inner_rtol;
+  for (int l = 0; l < LANES; ++l) {
+    cudaGraphNode_t prev = nullptr;
+    for (int p : lane[l]) {
+      Plan* P = plans[p];
+      cudaGraphNode_t n_pre, n_last, n_post;
+      GS_TRY(add_child(G, prev ? &prev : nullptr, P->cap_stream, [&](cudaStream_t c) -> gs_status {
+        if (o.x0_given) GS_CUDA(cudaMemcpyAsync(P->x64, x[p], P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, c));
+        GS_TRY(gather_sorted<double>(P, (const double2*)y[p], (double2*)P->y64, c));
+        k_set_params<<<1, 1, 0, c>>>(P->scal, tol2, (double)o.maxit, (double)o.max_outer, irt2);
+        GS_CUDA(cudaGetLastError());
+        return GS_OK;
+      }, &n_pre));
+      GS_TRY(add_solve_nodes(P, o.x0_given != 0, G, n_pre, &n_last));
+      GS_TRY(add_child(G, &n_last, P->cap_stream, [&](cudaStream_t c) -> gs_status {
+        GS_CUDA(cudaMemcpyAsync(x[p], P->x64, P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, c));
+        return GS_OK;
+      }, &n_post));
+      prev = n_post;
+    }
+  }
+  GS_CUDA(cudaGraphInstantiate(out, G, 0));
+  return GS_OK;
+}
+
+gs_status solve_batch_graph(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
+                            gs_solve_info* infos, cudaStream_t st) {
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d unsupported", dev);
+    return GS_EUNSUPPORTED;
+  }
+  std::vector<uint64_t> key;
+  key.reserve(6 + 3 * (size_t)B);
+  uint64_t bits[2];
+  std::memcpy(&bits[0], &o.tol, 8);
+  std::memcpy(&bits[1], &o.inner_rtol, 8);
+  key.insert(key.end(), {(uint64_t)B, (uint64_t)o.x0_given, bits[0], bits[1], (uint64_t)o.maxit,
+                         (uint64_t)o.max_outer});
+  bool measured = true;
+  for (int p = 0; p < B; ++p) {
+    key.push_back(plans[p]->uid);
+    key.push_back((uint64_t)(uintptr_t)y[p]);
+    key.push_back((uint64_t)(uintptr_t)x[p]);
+    measured = measured && plans[p]->last_iters > 0;
+  }
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  BatchGraph& bg = g_batch[dev];
+  if (!(bg.exec && bg.key == key && (bg.measured || !measured))) {
+    if (bg.exec) cudaGraphExecDestroy(bg.exec);
+    bg.exec = nullptr;
+    bg.key.clear();
+    gs_status s = build_batch_graph(plans, B, y, x, o, measured, st, &bg.exec);
+    if (s != GS_OK) {
+      bg.exec = nullptr;
+      return s;
+    }
+    bg.key = key;
+    bg.measured = measured;
+  }
+  GS_CUDA(cudaGraphLaunch(bg.exec, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  gs_status first = GS_OK;
+  for (int p = 0; p < B; ++p) {
+    gs_solve_info inf;
+    gs_status r = graph_solve_info(plans[p], o, &inf);
+    if (infos) infos[p] = inf;
+    if (r != GS_OK && first == GS_OK) first = r;
+  }
+  return first;
+}
+
 gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
                       gs_solve_info* infos, cudaStream_t st) {
+  bool all_graph = true;
+  for (int p = 0; p < B; ++p) all_graph = all_graph && graph_solve_ok(plans[p], o);
+  if (all_graph) return solve_batch_graph(plans, B, y, x, o, infos, st);
+  // options without a device-side solve (float64 mode, tol < 1e-7, tracing): one
+  // solve per problem, launched on 16 streams as they come free
   StreamPool* pool = nullptr;
   GS_TRY(get_pool(&pool));
   std::lock_guard<std::mutex> g(g_pool_mu);

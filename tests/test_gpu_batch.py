@@ -100,3 +100,51 @@ def test_graph_solve_from_given_start():
     assert info1["status"] == gs.GS_OK
     assert rel_normres(op, y, x1.cpu().numpy()) <= 1.1e-6
     assert info1["iterations"] < info0["iterations"]
+
+
+def test_batch_graph_repeats_bit_identically():
+    """The batch runs as one CUDA graph: the first call schedules by a common
+    iteration guess, the second rebuilds the schedule from the measured iteration
+    counts, the third reuses the cached graph; all three give the same x."""
+    probs = small_batch(8)
+    plans = [make_plan(pr) for pr in probs]
+    g = synth.rng(12)
+    ys = []
+    for pr, pl in zip(probs, plans):
+        yc = pl.T(torch.tensor(pr.x_true, device="cuda")).cpu().numpy()
+        ys.append(torch.tensor(yc + 1e-3 * synth.complex_gaussian(yc.size, g), device="cuda"))
+    outs = []
+    for _ in range(3):
+        xs = [torch.zeros(p.ncoef, dtype=torch.complex128, device="cuda") for p in plans]
+        infos = gs.gs_solve_batch([p.handle for p in plans], ys, xs, tol=1e-6, maxit=4000)
+        assert all(i["status"] == gs.GS_OK and i["rel_normres"] <= 1e-6 for i in infos), infos
+        outs.append(xs)
+    for a, b in zip(outs[0], outs[2]):
+        assert torch.equal(a, b)
+    for a, b in zip(outs[1], outs[2]):
+        assert torch.equal(a, b)
+
+
+def test_batch_from_learned_starts():
+    """gs_solve_batch_learned: each problem starts from the network's output (here
+    the untrained net, i.e. the density-compensated adjoint) and meets the
+    tolerance by the oracle's float64 residual."""
+    J = 5
+    N = 2**J
+    xi, mu = synth.radial_2d(64, 128, 0.5)
+    op = Operator2D(Basis1D(4, J), xi, mu)
+    plans, ys, yn = [], [], []
+    for k in range(4):
+        gk = synth.rng(800 + k)
+        xs_true = synth.ellipse_phantom(N, gk) + 0j
+        yc = op.apply(xs_true)
+        y = yc + 0.01 * np.sqrt(np.mean(np.abs(yc) ** 2)) * synth.complex_gaussian(yc.size, gk)
+        plans.append(gs.Plan.plan_2d(xi, 4, J, weights=mu))
+        ys.append(torch.tensor(y, device="cuda"))
+        yn.append(y)
+    net = gs.Cnn(N, N, channels=8, depth=2, max_batch=1, seed=5)
+    xs = [torch.zeros(p.ncoef, dtype=torch.complex128, device="cuda") for p in plans]
+    infos = gs.gs_solve_batch_learned([p.handle for p in plans], net, ys, xs, tol=1e-6, maxit=4000)
+    for y, x, info in zip(yn, xs, infos):
+        assert info["status"] == gs.GS_OK, info
+        assert rel_normres(op, y, x.cpu().numpy()) <= 1.1e-6
