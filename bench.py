@@ -391,9 +391,9 @@ def batch_bench(count, dev):
                                device=dev))
     xs = [torch.zeros(pl.ncoef, dtype=torch.complex128, device=dev) for pl in plans]
     handles = [pl.handle for pl in plans]
-    # warm-up: the first call builds the batch graph on a common iteration guess, the
-    # second rebuilds its schedule from the measured iteration counts; the timed call
-    # relaunches that graph
+    # warm-up: the first call builds each problem's solve graph and schedules the
+    # streams on a common iteration guess; the second schedules on the measured
+    # iteration counts, as the timed call does
     t0 = time.perf_counter()
     gs.gs_solve_batch(handles, ys, xs, tol=TOL, maxit=5000)
     t_first = time.perf_counter() - t0
@@ -419,7 +419,7 @@ def batch_bench(count, dev):
     return {"problems": count, "value": count / t_batch, "unit": "reconstructions/s", "seconds": t_batch,
             "one_at_a_time": {"value": count / t_seq, "seconds": t_seq}, "converged": ok,
             "iterations_total": int(sum(i["iterations"] for i in infos)), "init_s": init_s,
-            "first_call_s": t_first, "launch": "one CUDA graph per batch call (16 chains, longest first)",
+            "first_call_s": t_first, "launch": "one CUDA graph per problem, assigned to 16 streams longest-first by measured iterations",
             "workload": "mixed batch: 1D db2/db4 J 8..13 jittered + 2D db4 J 6..8 jittered/spiral, "
                         "oversampling 2..4, tol 1e-6, mixed precision"}
 
@@ -491,7 +491,7 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
     bplans = [gs.Plan.plan_2d(xi, P_VM, J, weights=mu) for _ in range(ntest)]
     bh = [p.handle for p in bplans]
     bx = [torch.zeros(plan.ncoef, dtype=torch.complex128, device=dev) for _ in range(ntest)]
-    for _ in range(2):  # graph build, then the schedule from measured iterations
+    for _ in range(2):  # graph builds, then the schedule from measured iterations
         gs.gs_solve_batch_learned(bh, net, tests, bx, tol=TOL, maxit=5000)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

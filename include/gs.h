@@ -79,6 +79,12 @@ typedef struct {
                    most; a tile's samples split into near-equal items (load balance).
                    > 0: that size; 0: 512; -1: autotune at plan time (times float32
                    T and T^H for sizes 128..1024 and keeps the fastest) [0] */
+  int lattice;  /* NFFT path on the lattice (1/sigma) Z^d: when sigma xi is an integer for
+                   every sample and dimension (e.g. the uniform grids of Sec. 3.2, tensor
+                   grids in 2D), T and T^H are exact FFTs: the grid value of each sample is
+                   picked (T) or folded in (T^H) with no window and no deapodisation.
+                   0: use it when the samples allow; 1: never; 2: require it (GS_EINVAL
+                   otherwise) [0] */
 } gs_opts;
 
 /* Build a 1D plan: the representation of T (paper: Freq2Wave(xi, "dbp", J[, bandwidth]),
@@ -175,17 +181,15 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
                    gs_solve_info* info, void* stream);
 
 /* B independent least-squares solves (one plan each, plans distinct) with the
- * options of gs_solve.  With GS_SOLVE_MIXED and tol >= 1e-7 the whole batch runs
- * as ONE CUDA graph launched on `stream`: 16 independent chains of whole solves
- * (each solve with its nested while-conditional nodes: refinement passes around
- * CG iterations, float64 residual and stop test on the device), problems assigned
- * to chains longest-first by estimated cost (CG iterations of the plan's previous
- * solve times a per-iteration time model), no host involvement until the graph has
- * finished.  The instantiated graph is cached while the same plans, buffers and
- * options recur (rebuilt once when measured iteration counts first become
- * available).  Other options run gs_solve per problem on 16 library-owned streams.
- * y[i], x[i] as in gs_solve; infos (host, B entries) may be NULL.  Returns the
- * first non-OK status of any problem (GS_ENOTCONV included). */
+ * options of gs_solve.  With GS_SOLVE_MIXED and tol >= 1e-7 each solve runs as one
+ * CUDA graph (nested while-conditional nodes: refinement passes around CG
+ * iterations, float64 residual and stop test on the device); the B graph launches
+ * are assigned up front to 16 library-owned streams, ordered after `stream`, by
+ * longest-processing-time-first on an estimated cost (CG iterations of the plan's
+ * previous solve times a per-iteration time model), and the call waits once, when
+ * all have finished.  Other options run gs_solve per problem on those streams as
+ * they come free.  y[i], x[i] as in gs_solve; infos (host, B entries) may be NULL.
+ * Returns the first non-OK status of any problem (GS_ENOTCONV included). */
 gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
                          const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
 

@@ -19,7 +19,7 @@ GS_SOLVE_FP64, GS_SOLVE_MIXED = 0, 1
 
 class GsOpts(ctypes.Structure):
     _fields_ = [("kb_m_hi", ctypes.c_int), ("kb_m_lo", ctypes.c_int), ("sigma", ctypes.c_int),
-                ("direct", ctypes.c_int), ("chunk", ctypes.c_int)]
+                ("direct", ctypes.c_int), ("chunk", ctypes.c_int), ("lattice", ctypes.c_int)]
 
 
 class GsSolveOpts(ctypes.Structure):
@@ -122,8 +122,8 @@ def _f64(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _opts(kb_m_hi=8, kb_m_lo=4, sigma=2, direct=-1, chunk=0):
-    return GsOpts(kb_m_hi, kb_m_lo, sigma, direct, chunk)
+def _opts(kb_m_hi=8, kb_m_lo=4, sigma=2, direct=-1, chunk=0, lattice=0):
+    return GsOpts(kb_m_hi, kb_m_lo, sigma, direct, chunk, lattice)
 
 
 def gs_plan_1d(xi, p: int, J: int, bandwidth: float = 0.0, weights=None, stream=None, **opts):

@@ -188,12 +188,12 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
         set_error("weights[%lld] is negative or not finite", (long long)i);
         return GS_EINVAL;
       }
-  gs_opts o = {8, 4, 2, -1, 0};
+  gs_opts o = {8, 4, 2, -1, 0, 0};
   if (opts) o = *opts;
   if (o.kb_m_hi < 2 || o.kb_m_hi > 8 || o.kb_m_lo < 2 || o.kb_m_lo > 8 || (o.sigma != 2 && o.sigma != 4) ||
-      o.chunk < -1 || o.chunk > (1 << 20)) {
-    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..8), sigma = %d (2 or 4), chunk = %d (-1..2^20)",
-              o.kb_m_hi, o.kb_m_lo, o.sigma, o.chunk);
+      o.chunk < -1 || o.chunk > (1 << 20) || o.lattice < 0 || o.lattice > 2) {
+    set_error("bad options: kb_m_hi = %d, kb_m_lo = %d (2..8), sigma = %d (2 or 4), chunk = %d (-1..2^20), "
+              "lattice = %d (0..2)", o.kb_m_hi, o.kb_m_lo, o.sigma, o.chunk, o.lattice);
     return GS_EINVAL;
   }
   gs_plan_s* h = new (std::nothrow) gs_plan_s();
@@ -239,6 +239,21 @@ static gs_status make_plan(gs_plan* out, int dims, const double* xi, int64_t M, 
     // direct evaluation (one thread per sample or coefficient, a sincos per entry)
     // only for tiny problems; the NFFT path is faster from ~2^16 entries
     P->direct = (!nfft_ok || (double)M * (double)P->ncoef <= 65536.0) ? 1 : 0;
+  }
+  if (!P->direct && o.lattice != 1) {
+    // Sec. 3.2: samples on the lattice (1/sigma) Z^d (exactly, in double) make the
+    // NDFT an FFT; sigma is a power of two, so sigma xi is exact
+    bool on = true;
+    for (int64_t i = 0; i < M * dims && on; ++i) {
+      const double v = xi[i] * (double)o.sigma;
+      on = (v == std::rint(v));
+    }
+    P->lattice = on ? 1 : 0;
+  }
+  if (o.lattice == 2 && !P->lattice) {
+    set_error("lattice = 2: the samples are not all on the lattice (1/sigma) Z^d of an NFFT-path plan");
+    delete h;
+    return GS_EINVAL;
   }
   if (!build_constants(p, &P->k)) {
     set_error("boundary construction failed for p = %d", p);

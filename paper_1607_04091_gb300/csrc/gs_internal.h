@@ -114,6 +114,7 @@ struct PrecData {
 
 struct Plan {
   int dims = 1, p = 1, J = 0, b = 0, sigma = 2, direct = 0;
+  int lattice = 0;  // 1: every sigma xi is an integer: exact pick / fold instead of KB windows
   int m_hi = 8, m_lo = 4;
   double bandwidth = 0.0;
   int64_t M = 0, N = 0, n = 0, ncoef = 0;
@@ -267,6 +268,14 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
                          bool df = false);  // float64: double-float arithmetic (k_interp2d_df)
 template <typename R>
 gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, C<R>* part, cudaStream_t st);
+// exact lattice path (lattice.cu): T's per-sample pick after the forward passes,
+// T^H's folds into the grid, side lines and boundary channels before the inverse
+// passes (same tables and workspaces as the NFFT path)
+template <typename R>
+gs_status lattice_pick(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t* perm, cudaStream_t st,
+                       double* norm_part, const C<R>* hrows);
+template <typename R>
+gs_status lattice_fold(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* perm, cudaStream_t st);
 template <typename R>
 gs_status gather_sorted(Plan* P, const C<R>* y_user, C<R>* y_sorted, cudaStream_t st);
 template <typename R>

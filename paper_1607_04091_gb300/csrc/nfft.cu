@@ -919,9 +919,11 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
       GS_LAUNCH(pname<R>("fwd1d_fft<f32>", "fwd1d_fft<f64>"), st,
                 k_fwd1d_fft<R><<<1, fft_threads(1, n), sh, st>>>(x, D.deap, N, n, logn, D.tw, D.grid));
     }
-    GS_LAUNCH(pname<R>("interp1d<f32>", "interp1d<f64>"), st,
-              k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
-                                                             x, N, M, perm, y));
+    if (P->lattice) GS_TRY(lattice_pick<R>(P, D, x, y, perm, st, nullptr, nullptr));
+    else
+      GS_LAUNCH(pname<R>("interp1d<f32>", "interp1d<f64>"), st,
+                k_interp1d<R><<<(M + 255) / 256, 256, 0, st>>>(P->fl, D.frac, D.w, D.bf, b, D.grid, n, D.m, beta,
+                                                               x, N, M, perm, y));
   } else {
     // pass 1 (the x transforms of the rows), unless a CG direction update forms
     // them from those of s and of the previous p in pass 2
@@ -957,6 +959,9 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
   if (P->dims == 1) {
     const int warps = 4;
     size_t sh = (size_t)warps * (tile + 2 * m + b2) * sizeof(C<R>);
+    if (P->lattice) {
+      GS_TRY(lattice_fold<R>(P, D, y, perm, st));
+    } else {
     GS_LAUNCH(pname<R>("spread1d<f32>", "spread1d<f64>"), st,
               k_spread1d<R><<<P->nwork, warps * 32, sh, st>>>(P->work, P->fl, D.frac, D.w, D.bf, b, y, perm, tile,
                                                               m, beta, part, D.part_stride));
@@ -966,6 +971,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
     if (b2 > 0)
       GS_LAUNCH(pname<R>("reduce_chan<f32>", "reduce_chan<f64>"), st,
                 k_reduce_chan<R><<<b2, 256, 0, st>>>(part, D.part_stride, tile + 2 * m, b2, P->nwork, D.corner));
+    }
     if (n >= FOUR_STEP_N) {
       const int logn1 = logn / 2, logn2 = logn - logn1, n1 = 1 << logn1, n2 = 1 << logn2;
       GS_LAUNCH(pname<R>("adj1d_rows<f32>", "adj1d_rows<f64>"), st,
@@ -983,11 +989,12 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
   } else {
     const int PW = tile + 2 * m;
     const int wsz = PW * PW + 2 * b2 * PW;
-    gs_status s = launch_spread2d<R>(P, D, y, perm, part, st);
+    const bool lat = P->lattice != 0;
+    gs_status s = lat ? lattice_fold<R>(P, D, y, perm, st) : launch_spread2d<R>(P, D, y, perm, part, st);
     if (s != GS_OK) return s;
     // the three reductions of the partials read the same input: side segments and
     // corners on two side branches, the grid on st
-    if (b2 > 0) {
+    if (b2 > 0 && !lat) {
       GS_TRY(fork_aux(P, st, 0));
       GS_TRY(fork_aux(P, st, 1));
       cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
@@ -1004,7 +1011,8 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
                                                            D.corner));
     }
     dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    if (tile == 16 && P->nbx >= 3)
+    if (lat) {
+    } else if (tile == 16 && P->nbx >= 3)
       GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
                 k_reduce2d_grid16<R><<<rg, 256, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, m, n,
                                                          D.grid));
@@ -1012,7 +1020,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
       GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
                 k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m, n,
                                                       D.grid));
-    if (b2 > 0) {
+    if (b2 > 0 && !lat) {
       GS_CUDA(cudaGetLastError());
       GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
     }
@@ -1027,7 +1035,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
     size_t sh1 = (size_t)rows * n * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
-    if (b2 > 0) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
+    if (b2 > 0 && !lat) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
     const CgStep<R> cgv =
         cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr, nullptr, nullptr};

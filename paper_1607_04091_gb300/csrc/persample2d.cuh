@@ -867,6 +867,7 @@ gs_status launch_interp2d(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const
   using namespace dev;
   const int b = P->b, b2 = 2 * b, tile = P->tile;
   if (P->nwork == 0) return GS_OK;
+  if (P->lattice) return lattice_pick<R>(P, D, x, y, perm, st, norm_part, hrows);
   const C<R>* hb = hrows ? hrows : D.hbuf;
   return dispatch_wb(2 * D.m, b2, [&](auto wc, auto bc) -> gs_status {
     constexpr int W = decltype(wc)::value;

@@ -897,122 +897,62 @@ gs_status get_pool(StreamPool** out) {
 }
 }  // namespace
 
-// ---------------------------------------------------------------- one graph per batch
-// A batch of mixed solves runs as ONE CUDA graph: LANES dependency chains, each a
-// sequence of whole solves (data gather and parameters, the solve's nodes with
-// its nested while loops, the copy of the result), the chains independent of one
-// another.  Problems go to chains by longest-processing-time-first: sorted by
-// estimated cost, each to the chain with the least work so far.  The cost of a
+// ---------------------------------------------------------------- batch schedule
+// A batch of mixed solves: each problem's whole solve is one CUDA graph (nested
+// while-conditional nodes), launched on one of POOL library-owned streams.  The
+// problems are assigned to streams up front by longest-processing-time-first:
+// sorted by estimated cost, each to the stream with the least work so far, so the
+// host enqueues every launch at once and waits only at the end.  The cost of a
 // solve is its CG iterations times a per-iteration time model (a fixed ~40 us of
 // small kernels plus terms in M and the coefficient count); the iterations are
-// those of the plan's previous solve when every plan has one (the schedule then
-// tunes itself on measured counts), else a common guess.  The instantiated graph
-// is cached per device, keyed by the plans, buffers and options, and rebuilt once
-// when measured iteration counts first become available.
-constexpr int LANES = 16;
-struct BatchGraph {
-  std::vector<uint64_t> key;
-  cudaGraphExec_t exec = nullptr;
-  bool measured = false;
-};
-BatchGraph g_batch[64];
-
-double solve_cost(const Plan* P, bool measured) {
+// those of the plan's previous solve when it has one (the schedule tunes itself
+// on measured counts), else a common guess.  (One graph holding all solves as 16
+// chains was measured and is slower: 23.6 against ~35 problems/s on the
+// 512-problem batch, the chains' nested loops barely overlapping.)
+double solve_cost(const Plan* P) {
   const double per_it = 40.0 + (double)P->M / 3000.0 + (double)P->ncoef / 1000.0;  // us
-  return (measured ? (double)P->last_iters + 1.0 : 100.0) * per_it;
+  return ((P->last_iters > 0) ? (double)P->last_iters + 1.0 : 100.0) * per_it;
 }
 
-gs_status build_batch_graph(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
-                            bool measured, cudaStream_t st, cudaGraphExec_t* out) {
-  for (int p = 0; p < B; ++p)
-    if (!plans[p]->solve_kernels_warm) {
-      GS_TRY(warm_solve_kernels(plans[p], st));
-      plans[p]->solve_kernels_warm = true;
+gs_status solve_batch_graphs(Plan** plans, int B, const double* const* y, double* const* x,
+                             const gs_solve_opts& o, gs_solve_info* infos, cudaStream_t st) {
+  StreamPool* pool = nullptr;
+  GS_TRY(get_pool(&pool));
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  // graphs first (building one synchronises), then every launch
+  const int gi = o.x0_given ? 1 : 0;
+  for (int p = 0; p < B; ++p) {
+    Plan* P = plans[p];
+    if (P->solve_exec[gi]) continue;
+    gs_status s = build_solve_graph(P, gi == 1, st, &P->solve_exec[gi]);
+    if (s != GS_OK) {
+      P->solve_exec[gi] = nullptr;
+      P->solve_graph_failed = true;
+      return s;
     }
+  }
   std::vector<int> ord(B);
   std::vector<double> cost(B);
   for (int p = 0; p < B; ++p) {
     ord[p] = p;
-    cost[p] = solve_cost(plans[p], measured);
+    cost[p] = solve_cost(plans[p]);
   }
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  std::vector<std::vector<int>> lane(LANES);
-  std::vector<double> load(LANES, 0.0);
+  const int ns = B < POOL ? B : POOL;
+  std::vector<std::vector<int>> lane(ns);
+  std::vector<double> load(ns, 0.0);
   for (int p : ord) {
     const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
     lane[l].push_back(p);
     load[l] += cost[p];
   }
-  cudaGraph_t G = nullptr;
-  GS_CUDA(cudaGraphCreate(&G, 0));
-  struct Guard {
-    cudaGraph_t g;
-    ~Guard() {
-      if (g) cudaGraphDestroy(g);
-    }
-  } guard{G};
-  const double tol2 = o.tol * o.tol, irt2 = o.inner_rtol * o.inner_rtol;
-  for (int l = 0; l < LANES; ++l) {
-    cudaGraphNode_t prev = nullptr;
-    for (int p : lane[l]) {
-      Plan* P = plans[p];
-      cudaGraphNode_t n_pre, n_last, n_post;
-      GS_TRY(add_child(G, prev ? &prev : nullptr, P->cap_stream, [&](cudaStream_t c) -> gs_status {
-        if (o.x0_given) GS_CUDA(cudaMemcpyAsync(P->x64, x[p], P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, c));
-        GS_TRY(gather_sorted<double>(P, (const double2*)y[p], (double2*)P->y64, c));
-        k_set_params<<<1, 1, 0, c>>>(P->scal, tol2, (double)o.maxit, (double)o.max_outer, irt2);
-        GS_CUDA(cudaGetLastError());
-        return GS_OK;
-      }, &n_pre));
-      GS_TRY(add_solve_nodes(P, o.x0_given != 0, G, n_pre, &n_last));
-      GS_TRY(add_child(G, &n_last, P->cap_stream, [&](cudaStream_t c) -> gs_status {
-        GS_CUDA(cudaMemcpyAsync(x[p], P->x64, P->ncoef * sizeof(double2), cudaMemcpyDeviceToDevice, c));
-        return GS_OK;
-      }, &n_post));
-      prev = n_post;
-    }
+  GS_CUDA(cudaEventRecord(pool->start, st));
+  for (int i = 0; i < ns; ++i) {
+    GS_CUDA(cudaStreamWaitEvent(pool->s[i], pool->start, 0));
+    for (int p : lane[i]) GS_TRY(launch_solve_graph(plans[p], y[p], x[p], o, pool->s[i]));
+    GS_CUDA(cudaEventRecord(pool->done[i], pool->s[i]));
+    GS_CUDA(cudaStreamWaitEvent(st, pool->done[i], 0));
   }
-  GS_CUDA(cudaGraphInstantiate(out, G, 0));
-  return GS_OK;
-}
-
-gs_status solve_batch_graph(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
-                            gs_solve_info* infos, cudaStream_t st) {
-  int dev = 0;
-  GS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("device ordinal %d unsupported", dev);
-    return GS_EUNSUPPORTED;
-  }
-  std::vector<uint64_t> key;
-  key.reserve(6 + 3 * (size_t)B);
-  uint64_t bits[2];
-  std::memcpy(&bits[0], &o.tol, 8);
-  std::memcpy(&bits[1], &o.inner_rtol, 8);
-  key.insert(key.end(), {(uint64_t)B, (uint64_t)o.x0_given, bits[0], bits[1], (uint64_t)o.maxit,
-                         (uint64_t)o.max_outer});
-  bool measured = true;
-  for (int p = 0; p < B; ++p) {
-    key.push_back(plans[p]->uid);
-    key.push_back((uint64_t)(uintptr_t)y[p]);
-    key.push_back((uint64_t)(uintptr_t)x[p]);
-    measured = measured && plans[p]->last_iters > 0;
-  }
-  std::lock_guard<std::mutex> g(g_pool_mu);
-  BatchGraph& bg = g_batch[dev];
-  if (!(bg.exec && bg.key == key && (bg.measured || !measured))) {
-    if (bg.exec) cudaGraphExecDestroy(bg.exec);
-    bg.exec = nullptr;
-    bg.key.clear();
-    gs_status s = build_batch_graph(plans, B, y, x, o, measured, st, &bg.exec);
-    if (s != GS_OK) {
-      bg.exec = nullptr;
-      return s;
-    }
-    bg.key = key;
-    bg.measured = measured;
-  }
-  GS_CUDA(cudaGraphLaunch(bg.exec, st));
   GS_CUDA(cudaStreamSynchronize(st));
   gs_status first = GS_OK;
   for (int p = 0; p < B; ++p) {
@@ -1028,7 +968,7 @@ gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const
                       gs_solve_info* infos, cudaStream_t st) {
   bool all_graph = true;
   for (int p = 0; p < B; ++p) all_graph = all_graph && graph_solve_ok(plans[p], o);
-  if (all_graph) return solve_batch_graph(plans, B, y, x, o, infos, st);
+  if (all_graph) return solve_batch_graphs(plans, B, y, x, o, infos, st);
   // options without a device-side solve (float64 mode, tol < 1e-7, tracing): one
   // solve per problem, launched on 16 streams as they come free
   StreamPool* pool = nullptr;

@@ -282,12 +282,16 @@ __global__ void k_tables(const double* __restrict__ xs, const double* __restrict
 
 // deapodisation 1/psi(k), psi(k) = I0(m sqrt(beta^2 - (2 pi k/n)^2)), interior
 // indices only (boundary indices get 0 so the NFFT ignores them)
+// 1 / psi(k) of the interior coefficients (0 at the boundary indices); unit: 1
+// instead (the exact lattice path has no window to divide out)
 __global__ void k_deap(int64_t N, int b, int64_t n, int m, double beta, double* d64, float* d32,
-                       int which) {
+                       int which, int unit) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   double v = 0.0;
-  if (i >= b && i < N - b) {
+  if (unit) {
+    v = (i >= b && i < N - b) ? 1.0 : 0.0;
+  } else if (i >= b && i < N - b) {
     double k = (double)(i - N / 2);
     double a = 2.0 * M_PI * k / (double)n;
     double arg = (double)m * sqrt(beta * beta - a * a);
@@ -558,8 +562,10 @@ gs_status build_plan(Plan* P, const double* xi_host, const double* mu_host, cuda
                                              P->f.m, P->f.beta, P->f.win);
   if (P->d.win)
     k_win64<<<(tot + 127) / 128, 128, 0, st>>>(P->d.frac, M, dims, P->d.m, P->d.beta, P->d.win);
-  k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->d.m, P->d.beta, P->d.deap, nullptr, 0);
-  k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->f.m, P->f.beta, nullptr, P->f.deap, 1);
+  k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->d.m, P->d.beta, P->d.deap, nullptr, 0,
+                                             P->lattice);
+  k_deap<<<(P->N + 255) / 256, 256, 0, st>>>(P->N, P->b, P->n, P->f.m, P->f.beta, nullptr, P->f.deap, 1,
+                                             P->lattice);
   k_twiddle<<<(P->n / 2 + 255) / 256, 256, 0, st>>>(P->n, P->d.tw, P->f.tw);
   GS_CUDA(cudaGetLastError());
 

@@ -103,3 +103,16 @@ def test_nfft_path_beyond_the_grid_limits_is_unsupported():
     with pytest.raises(gs.GsError) as e:
         gs.gs_plan_2d(np.zeros((10, 2)), 2, 10, stream=_NoStream(), direct=0)
     assert e.value.status == gs.GS_EUNSUPPORTED
+
+
+def test_plan_lattice_option_validated_without_gpu():
+    # lattice = 2 requires every sigma xi to be an integer (Sec. 3.2 uniform grids);
+    # out-of-range values of the option are bad options
+    xi = np.linspace(-10, 10, 50) + 0.1
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(xi, 2, 5, direct=0, lattice=2, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+    assert b"lattice" in gs.load().gs_last_error_detail()
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_plan_1d(np.arange(-16, 16) / 2.0, 2, 5, direct=0, lattice=3, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL

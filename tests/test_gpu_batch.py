@@ -103,9 +103,9 @@ def test_graph_solve_from_given_start():
 
 
 def test_batch_graph_repeats_bit_identically():
-    """The batch runs as one CUDA graph: the first call schedules by a common
-    iteration guess, the second rebuilds the schedule from the measured iteration
-    counts, the third reuses the cached graph; all three give the same x."""
+    """The first batch call assigns the problems to streams on a common iteration
+    guess, later calls on the measured iteration counts of the previous solves:
+    the schedule changes, the results do not (each solve is deterministic)."""
     probs = small_batch(8)
     plans = [make_plan(pr) for pr in probs]
     g = synth.rng(12)
