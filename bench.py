@@ -23,6 +23,10 @@ import time
 
 import numpy as np
 
+# more hardware work queues than CUDA's default 8, so that the batch section's 16
+# solve streams do not share queues (a per-process setting, read at context creation)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -162,6 +166,56 @@ def oracle_time_per_iteration(xi, mu, y, sample=ORACLE_SAMPLE, min_s=3.0):
     return (t / reps) * (M / sample), reps
 
 
+def oracle_probe(threads):
+    """Oracle timings with `threads` BLAS/OpenMP threads (set by the caller's
+    environment before numpy loads): full FP64 CGLS solves of the 1D
+    configurations (Haar J=6 on the 128 integer frequencies, to 1e-12; db4 J=10
+    on 4096 jittered samples with Voronoi weights, to TOL) and the sampled
+    per-iteration time of the 2D radial workload."""
+    from oracle.operator import Basis1D, Operator1D
+    from oracle.solvers import cgls
+    from oracle.weights import voronoi_1d
+
+    out = {"threads": threads}
+    xi, xt = synth.haar_integers()
+    t0 = time.perf_counter()
+    op = Operator1D(Basis1D(1, 6), xi)
+    t1 = time.perf_counter()
+    y = op.apply(xt)
+    x, it, _ = cgls(op.apply, op.adjoint, y, tol=1e-12, maxit=1000)
+    t2 = time.perf_counter()
+    out["haar_J6"] = {"init_s": t1 - t0, "solve_s": t2 - t1, "iterations": it, "tol": 1e-12,
+                      "max_err": float(np.max(np.abs(x - xt)))}
+    g = synth.rng(1002)
+    xi = synth.jitter_1d(2048, g)
+    mu = voronoi_1d(xi, 2048.0)
+    xs = synth.piecewise_smooth(2**10, g) + 0j
+    t0 = time.perf_counter()
+    op = Operator1D(Basis1D(4, 10), xi, mu)
+    t1 = time.perf_counter()
+    y = op.apply(xs) + 1e-3 * synth.complex_gaussian(xi.size, g) * np.sqrt(mu)
+    x, it, _ = cgls(op.apply, op.adjoint, y, tol=TOL, maxit=5000)
+    t2 = time.perf_counter()
+    out["db4_J10_jitter"] = {"init_s": t1 - t0, "solve_s": t2 - t1, "iterations": it, "tol": TOL}
+    xi2, mu2, _, noise = workload()
+    tpi, reps = oracle_time_per_iteration(xi2, mu2, noise[0], min_s=2.0)
+    out["radial_J8_per_iteration_s"] = tpi
+    out["radial_J8_reps"] = reps
+    return out
+
+
+def oracle_probe_run(threads):
+    """oracle_probe in a fresh interpreter with the thread count fixed in its environment."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-probe", str(threads)],
+                       capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle probe failed: {r.stderr[-500:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 # ------------------------------------------------------------------ multi-rank timing
 def max_over_ranks(ms, dist=None, device="cpu"):
     """The largest of the ranks' `ms` (an all-reduce MAX; one process returns its own)."""
@@ -194,9 +248,15 @@ def main():
                     help="also train the warm-start CNN on this many method-generated pairs and time "
                          "zero / adjoint / learned starts and the learned + batched + mixed solve against "
                          "plain float64 CGLS on held-out problems (0: skip; single-GPU runs only)")
+    ap.add_argument("--table1", type=int, default=1,
+                    help="also time plan and solve on the five problem shapes of the paper's Table 1 (0: skip)")
     ap.add_argument("--probe-apply", type=int, default=0,
                     help="only run this many float32 T^H and T applies on the workload (for profilers)")
+    ap.add_argument("--oracle-probe", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_probe:
+        print(json.dumps(oracle_probe(args.oracle_probe)), flush=True)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -336,16 +396,26 @@ def main():
             fit.append(inf["iterations"])
         fp64 = {"value": 1e3 / np.mean(fe), "unit": UNIT, "iterations": fit, "ms_per_step": float(np.mean(fe))}
 
+    table1 = table1_bench(dev) if args.table1 and world == 1 else None
     batch = batch_bench(args.batch, dev) if args.batch > 0 and world == 1 else None
     learned = learned_bench(plan, xi, mu, args.learned, 16, dev) if args.learned > 0 and world == 1 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it_ref = fp64["iterations"][0] if fp64 else int(np.median(iters))
-        tpi, reps = oracle_time_per_iteration(xi, mu, ys[0].cpu().numpy())
-        cpu = {"value": 1.0 / (it_ref * tpi), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"FP64 oracle T and T^H on {ORACLE_SAMPLE} of {M} rows ({reps} reps), scaled by "
-                         f"M/{ORACLE_SAMPLE} and by the {it_ref} FP64 CGLS iterations of this workload"}
+        allc = oracle_probe_run(os.cpu_count())
+        one = oracle_probe_run(1)
+        tpi = allc["radial_J8_per_iteration_s"]
+        cpu = {"value": 1.0 / (it_ref * tpi), "unit": UNIT, "cores": allc["threads"], "kind": "oracle",
+               "sample": f"extrapolated: FP64 oracle T and T^H on {ORACLE_SAMPLE} of {M} rows "
+                         f"({allc['radial_J8_reps']} reps, {allc['threads']} BLAS threads), scaled by "
+                         f"M/{ORACLE_SAMPLE} and by the {it_ref} FP64 CGLS iterations of this workload",
+               "single_thread_value": 1.0 / (it_ref * one["radial_J8_per_iteration_s"]),
+               "full_solves": {"all_threads": {k: allc[k] for k in ("haar_J6", "db4_J10_jitter")},
+                               "one_thread": {k: one[k] for k in ("haar_J6", "db4_J10_jitter")},
+                               "threads": allc["threads"],
+                               "note": "timed whole oracle CGLS solves (not extrapolated) of the two 1D "
+                                       "configurations; init = building the dense T"}}
 
     if rank != 0:
         return
@@ -359,7 +429,8 @@ def main():
         "iterations": iters, "converged": ok, "rel_normres": [i["rel_normres"] for i in infos],
         "outer": [i["outer"] for i in infos],
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "apply": apply, "kernel_shares": shares,
-        "fp64_cgls": fp64, "batch": batch, "learned": learned, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "fp64_cgls": fp64, "batch": batch, "learned": learned, "table1": table1, "cpu_baseline": cpu,
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -521,6 +592,79 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
             "net": "6 conv3x3 layers 2-32-32-32-32-32-2, ReLU, residual, bf16 inference weights"}
 
 
+# Table 1 of the paper (Sec. 6.3): its GeneralizedSampling (Julia) timings on a
+# 2.6 GHz laptop, for context: (init s, sol s, iterations).  All db4.
+TABLE1 = [
+    ("Uniform 1D", "8192x4096", (0.34, 0.04, 12)),
+    ("Jitter 1D", "5463x2048", (0.23, 0.08, 20)),
+    ("Uniform 2D", "512^2x256^2", (0.15, 17.6, 16)),
+    ("Jitter 2D", "26244x32^2", (2.4, 2.4, 18)),
+    ("Spiral", "27681x32^2", (2.8, 2.2, 16)),
+]
+
+
+def table1_problem(name):
+    """Synthetic stand-ins of Table 1's sampling patterns at its sizes (the paper
+    does not give its jitter or spiral parameters): (dims, p, J, xi, bandwidth)."""
+    g = synth.rng(6001)
+    if name == "Uniform 1D":
+        return 1, 4, 12, synth.grid_1d(8192, 0.5), 0.0
+    if name == "Jitter 1D":
+        xi = synth.jitter_grid_1d(5463, 0.75, g)
+        return 1, 4, 11, xi, float(np.ceil(np.abs(xi).max()))
+    if name == "Uniform 2D":
+        return 2, 4, 8, synth.uniform_2d(512, 0.5), 0.0
+    if name == "Jitter 2D":
+        return 2, 4, 5, synth.jitter_grid_2d(162, 0.5, g), 0.0
+    return 2, 4, 5, synth.spiral_2d(27681, 0.5), 0.0
+
+
+def table1_bench(dev, reps=3):
+    """Each Table 1 shape: plan time (the paper's "init"), the mixed-precision solve
+    to TOL and the float64 CGLS to TOL (the paper's "sol"), with iterations and time
+    per iteration; data T x* + 1% noise, x* piecewise smooth (1D) or 10 ellipses (2D)."""
+    import torch
+    import paper_1607_04091_gb300 as gs
+
+    out = []
+    for name, size, paper in TABLE1:
+        dims, p, Jt, xi, bw = table1_problem(name)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = (gs.Plan.plan_1d(xi, p, Jt, bandwidth=bw) if dims == 1 else gs.Plan.plan_2d(xi, p, Jt))
+        torch.cuda.synchronize()
+        init_ms = (time.perf_counter() - t0) * 1e3
+        g = synth.rng(6002)
+        N = 2**Jt
+        xs = (synth.piecewise_smooth(N, g) if dims == 1 else synth.ellipse_phantom(N, g)) + 0j
+        yc = plan.T(torch.tensor(xs, device=dev)).cpu().numpy()
+        y = torch.tensor(yc + 0.01 * np.sqrt(np.mean(np.abs(yc) ** 2)) * synth.complex_gaussian(yc.size, g),
+                         device=dev)
+        res = {}
+        for mode, key, nrep in [(gs.GS_SOLVE_MIXED, "mixed", reps), (gs.GS_SOLVE_FP64, "fp64", 1)]:
+            x = torch.zeros(plan.ncoef, dtype=torch.complex128, device=dev)
+            gs.gs_solve(plan.handle, y, x, tol=TOL, maxit=5000, mode=mode)  # warm-up (graph build)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms, it = [], []
+            for _ in range(nrep):
+                x.zero_()
+                a.record()
+                info = gs.gs_solve(plan.handle, y, x, tol=TOL, maxit=5000, mode=mode)
+                b.record()
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+                it.append(info["iterations"])
+            res[key] = {"ms": float(np.median(ms)), "iterations": int(np.median(it)),
+                        "ms_per_iteration": float(np.median(ms)) / max(1, int(np.median(it))),
+                        "rel_normres": info["rel_normres"], "status": info["status"]}
+        out.append({"problem": name, "size": size, "M": int(xi.shape[0]), "J": Jt,
+                    "path": "exact lattice FFT" if np.all(2 * xi == np.rint(2 * xi)) else "NFFT",
+                    "init_ms": init_ms, **res,
+                    "paper_julia_laptop": {"init_s": paper[0], "sol_s": paper[1], "iterations": paper[2]}})
+        del plan
+    return out
+
+
 def apply_timings(gs, plan, flush, M, N, b, peak, reps=20):
     """float32 T and T^H applies through the public API (caller's sample order):
     warm = `reps` back-to-back applies, cold = L2 flushed before each (median);
@@ -605,8 +749,9 @@ def reference_arm(args, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"each step: FP64 oracle T and T^H on {ORACLE_SAMPLE} of {xi.shape[0]} "
-                                       f"rows, scaled by M/{ORACLE_SAMPLE} and by {it_ref} CGLS iterations"},
+                             "sample": f"extrapolated, each step: FP64 oracle T and T^H on {ORACLE_SAMPLE} of "
+                                       f"{xi.shape[0]} rows, scaled by M/{ORACLE_SAMPLE} and by {it_ref} CGLS "
+                                       f"iterations (numpy's default BLAS threads)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -947,9 +947,16 @@ gs_status solve_batch_graphs(Plan** plans, int B, const double* const* y, double
     load[l] += cost[p];
   }
   GS_CUDA(cudaEventRecord(pool->start, st));
+  for (int i = 0; i < ns; ++i) GS_CUDA(cudaStreamWaitEvent(pool->s[i], pool->start, 0));
+  // round-robin over the streams, so that streams sharing a hardware queue
+  // interleave their solves in schedule order instead of one stream's whole list
+  // queueing ahead of the other's
+  size_t depth = 0;
+  for (int i = 0; i < ns; ++i) depth = std::max(depth, lane[i].size());
+  for (size_t r = 0; r < depth; ++r)
+    for (int i = 0; i < ns; ++i)
+      if (r < lane[i].size()) GS_TRY(launch_solve_graph(plans[lane[i][r]], y[lane[i][r]], x[lane[i][r]], o, pool->s[i]));
   for (int i = 0; i < ns; ++i) {
-    GS_CUDA(cudaStreamWaitEvent(pool->s[i], pool->start, 0));
-    for (int p : lane[i]) GS_TRY(launch_solve_graph(plans[p], y[p], x[p], o, pool->s[i]));
     GS_CUDA(cudaEventRecord(pool->done[i], pool->s[i]));
     GS_CUDA(cudaStreamWaitEvent(st, pool->done[i], 0));
   }

@@ -15,6 +15,7 @@ Workloads (M samples, N = 2^J coefficients per dimension):
                      polar cell areas |r| dr dtheta                       (seed 1003)
   ellipse_phantom    X* = 2^-J * sum of 10 random ellipses at cell centres
   jitter_2d, spiral_2d, batch_specs   mixed batch of 512 problems       (seed 4004)
+  grid_1d, uniform_2d, jitter_grid_1d, jitter_grid_2d   the shapes of Table 1
 """
 from dataclasses import dataclass
 
@@ -87,6 +88,29 @@ def spiral_2d(M: int, spacing: float = 1.0) -> np.ndarray:
         # arc element ds = sqrt(r^2 + a^2) dtheta
         th += spacing / np.sqrt(r * r + a * a)
     return pts
+
+
+def grid_1d(M: int, eps: float) -> np.ndarray:
+    """The uniform grid xi_m = eps (m - 1 - M/2), m = 1..M (the paper's grid(M, eps))."""
+    return eps * (np.arange(1, M + 1) - 1 - M / 2)
+
+
+def uniform_2d(P: int, eps: float) -> np.ndarray:
+    """Tensor grid of grid_1d(P, eps) with itself, (P^2, 2), x varying fastest."""
+    k = grid_1d(P, eps)
+    X, Y = np.meshgrid(k, k)
+    return np.stack([X.ravel(), Y.ravel()], axis=1)
+
+
+def jitter_grid_1d(M: int, spacing: float, g: np.random.Generator) -> np.ndarray:
+    """M points spacing apart, centred on 0, each moved by U(-spacing/2, spacing/2)."""
+    return grid_1d(M, spacing) + spacing * (0.5 + g.uniform(-0.5, 0.5, size=M))
+
+
+def jitter_grid_2d(P: int, spacing: float, g: np.random.Generator) -> np.ndarray:
+    """P x P points spacing apart, centred on 0, each coordinate moved by U(-spacing/4, spacing/4)."""
+    xi = uniform_2d(P, spacing) + 0.5 * spacing
+    return xi + g.uniform(-0.25 * spacing, 0.25 * spacing, size=xi.shape)
 
 
 def ellipse_phantom(N: int, g: np.random.Generator, count: int = 10) -> np.ndarray:
