@@ -193,6 +193,18 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
 gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
                          const gs_solve_opts* opts, gs_solve_info* infos, void* stream);
 
+/* 2D density weights (App. B, eq. Voronoi_tesselation): mu[m] = area of the
+ * Voronoi cell of xi_m within Y_K = [-K, K]^2, and *delta (may be NULL) = the
+ * largest distance from a point of Y_K to its nearest sample (the density of
+ * App. B, attained at a cell vertex).  Exact cells, computed on the GPU (one thread
+ * per sample clipping the square by the bisectors of nearby samples, stopped by
+ * the security radius).  xi host M x 2 interleaved, every coordinate within
+ * [-K, K] (GS_EINVAL otherwise); mu host M.  Repeated points share one cell each
+ * in full (their bisector is empty).  Synchronises `stream`; allocates and frees
+ * its own device memory.  GS_EUNSUPPORTED if a cell needs more than 64 vertices.
+ * The result suits gs_plan_2d's weights. */
+gs_status gs_voronoi_2d(const double* xi, int64_t M, double K, double* mu, double* delta, void* stream);
+
 /* ---- Learned warm start (an addition beside the paper's method) ----------
  * A residual CNN x0 = u + f(u) on the 2-channel image (real, imaginary part) of
  * u = T^H y, pixel (j, i) = coefficient i + N j, images NCHW float32.  f is

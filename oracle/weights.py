@@ -49,26 +49,32 @@ def _area(poly):
     return 0.5 * abs(s)
 
 
-def voronoi_cells_2d(xi, K: float):
-    """App. B: the Voronoi cell of each point within Y_K = [-K, K]^2, written out
-    from its definition: the points of Y_K no farther from xi_i than from any other
-    xi_j, i.e. Y_K clipped by the half-plane |x - xi_i| <= |x - xi_j| of every j
-    (O(M^2); small inputs only).  Returns a list of vertex lists."""
+def voronoi_cell_2d(xi, i: int, K: float):
+    """App. B: the Voronoi cell of xi_i within Y_K = [-K, K]^2, written out from its
+    definition: the points of Y_K no farther from xi_i than from any other xi_j,
+    i.e. Y_K clipped by the half-plane |x - xi_i| <= |x - xi_j| of every j (O(M)).
+    Returns its vertex list."""
     xi = np.asarray(xi, dtype=np.float64)
-    cells = []
-    for i in range(xi.shape[0]):
-        poly = [(-K, -K), (K, -K), (K, K), (-K, K)]
-        pi = xi[i]
-        for j in range(xi.shape[0]):
-            if j == i or not poly:
-                continue
-            pj = xi[j]
-            # |x - pi|^2 <= |x - pj|^2  <=>  2 (pj - pi) . x <= |pj|^2 - |pi|^2
-            a, b = 2.0 * (pj[0] - pi[0]), 2.0 * (pj[1] - pi[1])
-            c = pj[0] ** 2 + pj[1] ** 2 - pi[0] ** 2 - pi[1] ** 2
-            poly = _clip(poly, a, b, c)
-        cells.append(poly)
-    return cells
+    poly = [(-K, -K), (K, -K), (K, K), (-K, K)]
+    pi = xi[i]
+    for j in range(xi.shape[0]):
+        if j == i or not poly:
+            continue
+        pj = xi[j]
+        # |x - pi|^2 <= |x - pj|^2  <=>  2 (pj - pi) . x <= |pj|^2 - |pi|^2
+        a, b = 2.0 * (pj[0] - pi[0]), 2.0 * (pj[1] - pi[1])
+        c = pj[0] ** 2 + pj[1] ** 2 - pi[0] ** 2 - pi[1] ** 2
+        poly = _clip(poly, a, b, c)
+    return poly
+
+
+def cell_area(poly) -> float:
+    return _area(poly) if len(poly) >= 3 else 0.0
+
+
+def voronoi_cells_2d(xi, K: float):
+    """Every cell of voronoi_cell_2d (O(M^2); small inputs only)."""
+    return [voronoi_cell_2d(xi, i, K) for i in range(np.asarray(xi).shape[0])]
 
 
 def voronoi_2d(xi, K: float):

@@ -43,7 +43,7 @@ EXPORTS = ["gs_plan_1d", "gs_plan_2d", "gs_plan_destroy", "gs_plan_sizes", "gs_a
            "gs_apply_TH_noalloc", "gs_solve_batch", "gs_cnn_create", "gs_cnn_destroy", "gs_cnn_forward",
            "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights", "gs_cnn_set_weights", "gs_solve_learned", "gs_solve_batch_learned", "gs_cnn_pair",
            "gs_solve", "gs_boundary_constants", "gs_profile", "gs_profile_report", "gs_strerror",
-           "gs_last_error_detail"]
+           "gs_last_error_detail", "gs_voronoi_2d"]
 
 
 def load(path: str = LIB):
@@ -92,6 +92,8 @@ def load(path: str = LIB):
                                            ctypes.POINTER(vp), ctypes.POINTER(GsSolveOpts),
                                            ctypes.POINTER(GsSolveInfo), vp]
     lib.gs_cnn_pair.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.gs_voronoi_2d.argtypes = [dp, i64, ctypes.c_double, dp, dp, vp]
+    lib.gs_voronoi_2d.restype = ctypes.c_int
     for f in ["gs_cnn_create", "gs_cnn_forward", "gs_cnn_train_step", "gs_cnn_gradients", "gs_cnn_weights",
               "gs_cnn_set_weights", "gs_solve_learned", "gs_solve_batch_learned", "gs_cnn_pair"]:
         getattr(lib, f).restype = ctypes.c_int
@@ -415,6 +417,17 @@ def gs_solve_batch_learned(plans, net, ys, xs, tol=1e-6, maxit=1000, mode=GS_SOL
         _check(st, "gs_solve_batch_learned")
     return [{"iterations": i.iterations, "outer": i.outer, "rel_normres": i.rel_normres, "rel_res": i.rel_res,
              "status": i.status} for i in infos]
+
+
+def gs_voronoi_2d(xi, K: float, stream=None):
+    """(mu, delta): 2D Voronoi cell areas of the samples within [-K, K]^2 and the density."""
+    xa, xp = _f64(xi)
+    M = xa.shape[0]
+    mu = np.empty(M)
+    delta = ctypes.c_double()
+    _check(load().gs_voronoi_2d(xp, M, float(K), mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.byref(delta), _stream(stream)), "gs_voronoi_2d")
+    return mu, delta.value
 
 
 def gs_cnn_pair(plan, y, x=None, stream=None):

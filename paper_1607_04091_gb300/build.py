@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT, "libgs.so")
 SOURCES = ["host_constants.cpp", "tables.cu", "nfft.cu", "persample2d_f32.cu", "persample2d_f64.cu",
-           "direct.cu", "solve.cu", "capi.cu", "noalloc.cu", "cnn.cu", "lattice.cu"]
+           "direct.cu", "solve.cu", "capi.cu", "noalloc.cu", "cnn.cu", "lattice.cu",
+           "voronoi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

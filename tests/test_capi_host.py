@@ -116,3 +116,13 @@ def test_plan_lattice_option_validated_without_gpu():
     with pytest.raises(gs.GsError) as e:
         gs.gs_plan_1d(np.arange(-16, 16) / 2.0, 2, 5, direct=0, lattice=3, stream=_NoStream())
     assert e.value.status == gs.GS_EINVAL
+
+
+def test_voronoi_2d_validates_without_gpu():
+    # every coordinate must lie in [-K, K]; K > 0
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_voronoi_2d(np.array([[0.0, 0.0], [3.0, 0.0]]), 2.0, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL
+    with pytest.raises(gs.GsError) as e:
+        gs.gs_voronoi_2d(np.array([[0.0, 0.0]]), 0.0, stream=_NoStream())
+    assert e.value.status == gs.GS_EINVAL

@@ -322,3 +322,51 @@ def test_golden_files_match_their_cases(name):
     assert np.max(np.abs(op.apply(c["x"]) - gold["T"][:32])) <= 1e-13 * np.max(np.abs(gold["T"]))
     n = (2 ** c["J"]) ** 2 if c["coefs"] is None else c["coefs"].size
     assert gold["TH"].shape == (n,) and np.all(np.isfinite(gold["TH"]))
+
+
+# ------------------------------------------------------------------ 2D Voronoi weights (App. B)
+
+
+def test_voronoi_2d_hand_worked():
+    from oracle.weights import voronoi_2d
+
+    # four points at (+-1, +-1) in [-2, 2]^2: each cell is a quadrant of area 4; the
+    # farthest point of Y_K from its nearest sample is a corner, at distance sqrt2
+    mu, delta = voronoi_2d(np.array([[1.0, 1.0], [-1.0, 1.0], [-1.0, -1.0], [1.0, -1.0]]), 2.0)
+    assert np.allclose(mu, 4.0, rtol=0, atol=1e-14) and abs(delta - np.sqrt(2.0)) < 1e-14
+    # (0, 0) and (2, 0) in [-2, 2]^2: the bisector x = 1 splits the square 12 : 4;
+    # delta = |(-2, 2) - (0, 0)| = 2 sqrt2 (the right cell's farthest vertex is sqrt5 away)
+    mu, delta = voronoi_2d(np.array([[0.0, 0.0], [2.0, 0.0]]), 2.0)
+    assert np.allclose(mu, [12.0, 4.0], rtol=0, atol=1e-13) and abs(delta - 2.0 * np.sqrt(2.0)) < 1e-13
+
+
+def test_voronoi_2d_partition_and_equivariance():
+    from oracle.weights import voronoi_2d
+
+    g = np.random.default_rng(31)
+    xi = g.uniform(-4, 4, size=(120, 2))
+    mu, delta = voronoi_2d(xi, 4.5)
+    assert abs(mu.sum() - 81.0) < 1e-10 and np.all(mu > 0)  # the cells partition Y_K
+    pi = g.permutation(xi.shape[0])
+    mu2, delta2 = voronoi_2d(xi[pi], 4.5)
+    assert np.allclose(mu2, mu[pi], rtol=0, atol=1e-12) and abs(delta2 - delta) < 1e-12
+
+
+def test_voronoi_2d_reduces_to_1d_on_a_line():
+    # points on the x axis: every cell spans the full height 2K, so the 2D weight is
+    # 2K times the 1D Voronoi length of Sec. 4.1 (pinned on its own above)
+    from oracle.weights import voronoi_2d
+
+    g = np.random.default_rng(32)
+    x = g.uniform(-5, 5, size=25)
+    mu, _ = voronoi_2d(np.stack([x, np.zeros_like(x)], axis=1), 6.0)
+    assert np.allclose(mu, 12.0 * voronoi_1d(x, 6.0), rtol=0, atol=1e-11)
+
+
+def test_voronoi_2d_regular_grid():
+    from oracle.weights import voronoi_2d
+
+    k = np.arange(-3, 4) * 1.0  # 7 x 7 grid of spacing 1 in [-3.5, 3.5]^2
+    X, Y = np.meshgrid(k, k)
+    mu, delta = voronoi_2d(np.stack([X.ravel(), Y.ravel()], axis=1), 3.5)
+    assert np.allclose(mu, 1.0, rtol=0, atol=1e-13) and abs(delta - np.sqrt(0.5)) < 1e-13
