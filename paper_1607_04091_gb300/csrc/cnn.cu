@@ -6,12 +6,15 @@
 // learned component, this is an addition beside the method.
 //
 // Layout: activations NCHW float32, weights [c_out][c_in][3][3] float32
-// (+ a bfloat16 copy), biases [c_out].  H and W must be multiples of 16.
+// (+ a bfloat16 copy), biases [c_out].  H and W must be multiples of 16.  The
+// convolutions and the weight gradient run on the tensor cores (bfloat16
+// operands, float32 accumulation; see k_conv3_tc).
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "gs_internal.h"
@@ -43,51 +46,144 @@ constexpr int CI_CHUNK = 8; // input channels staged per pass
 __device__ inline float wval(float v) { return v; }
 __device__ inline float wval(__nv_bfloat16 v) { return __bfloat162float(v); }
 
+// ---------------------------------------------------------------- tensor-core convolutions
+// The 3x3 convolutions and the weight gradient are implicit GEMMs on the tensor
+// cores (mma.sync m16n8k16, bfloat16 operands, float32 accumulation); operands
+// are gathered from a staged input tile through a table of per-k offsets (no
+// im2col buffer).  TERMS = 3 splits every operand x = hi + lo into two bfloat16
+// (hi = x rounded, lo = the remainder rounded) and sums hi*hi + hi*lo + lo*hi,
+// ~16 significant bits per product (training and the gradient check); TERMS = 1
+// is the plain bfloat16 product (inference with bfloat16 weights).
+namespace tcc {
+constexpr int HALO = (TS + 2) * (TS + 2);  // staged input tile with its 1-pixel border
+__device__ inline uint32_t pack(float lo_col, float hi_col) {  // two bf16, the lower k in the low half
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo_col, hi_col);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ inline void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+__device__ inline void mma16816(float* c, const uint32_t* a, const uint32_t* b) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// offset in the staged tile of k = c * 9 + tap (tap = 3 dy + dx).  Beyond K (the
+// padding of K to a multiple of 16): offset 0, a finite staged value, whose
+// product meets a zero weight (convolution) or lands in an output column that is
+// never stored (weight gradient).  Every gather adds at most 15 (TS + 2) + 15 to
+// an offset, which keeps it inside the Cin x 18 x 18 staged tile.
+__device__ inline int koffset(int k, int K) {
+  return k < K ? (k / 9) * HALO + ((k % 9) / 3) * (TS + 2) + (k % 3) : 0;
+}
+__host__ __device__ inline int kpad(int K) { return (K + 15) & ~15; }
+}  // namespace tcc
+
+template <typename WT>
+inline size_t conv_smem(int Cin, int CO, int terms) {
+  const int K = Cin * 9, Kp = tcc::kpad(K), NP = (CO + 7) / 8 * 8;
+  return (size_t)(Cin * tcc::HALO + 4) * sizeof(float) + (size_t)Kp * sizeof(int) +
+         (size_t)NP * (Kp / 2) * sizeof(uint32_t) * (terms == 3 ? 2 : 1);
+}
+
 // out[b][o][y][x] = bias[o] + sum_c sum_t w[o][c][t] in[b][c][y+dy-1][x+dx-1] (ReLU optional).
-// CTA = 16 x 16 pixels of one image, thread = one pixel, CO accumulators.
-template <int CO, typename WT>
-__global__ void __launch_bounds__(256) k_conv3(const float* __restrict__ in, int Cin, const WT* __restrict__ w,
-                                               const float* __restrict__ bias, float* __restrict__ out, int H,
-                                               int W, int relu) {
-  __shared__ float sin_[CI_CHUNK][TS + 2][TS + 2];
-  __shared__ float sw[CI_CHUNK][9][CO];
-  const int tx = threadIdx.x % TS, ty = threadIdx.x / TS;
-  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, bimg = blockIdx.z;
-  const float* inb = in + (int64_t)bimg * Cin * H * W;
-  float acc[CO];
+// CTA = 16 x 16 pixels of one image, 8 warps; warp w takes pixel rows 2w, 2w + 1
+// (one m16 tile each: M = the 16 pixels of a row), N = output channels, K = c x tap.
+template <int CO, int TERMS, typename WT>
+__global__ void __launch_bounds__(256) k_conv3_tc(const float* __restrict__ in, int Cin, const WT* __restrict__ w,
+                                                  const float* __restrict__ bias, float* __restrict__ out, int H,
+                                                  int W, int relu) {
+  using namespace tcc;
+  constexpr int NT = (CO + 7) / 8, NP = NT * 8;
+  extern __shared__ __align__(16) unsigned char smc[];
+  const int K = Cin * 9, Kp = kpad(K), KH = Kp / 2;
+  float* sh = reinterpret_cast<float*>(smc);        // [Cin][18][18] (+4 floats of alignment)
+  int* koff = reinterpret_cast<int*>(sh + Cin * HALO + 4);
+  uint32_t* bh = reinterpret_cast<uint32_t*>(koff + Kp);  // [NP][Kp / 2] weight pairs, hi
+  uint32_t* bl = bh + NP * KH;                            // lo (TERMS == 3)
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  const int x0 = blockIdx.x * TS, y0 = blockIdx.y * TS, img = blockIdx.z;
+  const float* inb = in + (int64_t)img * Cin * H * W;
+  for (int i = tid; i < Cin * HALO; i += blockDim.x) {
+    const int c = i / HALO, r = i - c * HALO;
+    const int yy = y0 + r / (TS + 2) - 1, xx = x0 + r % (TS + 2) - 1;
+    sh[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? inb[((int64_t)c * H + yy) * W + xx] : 0.0f;
+  }
+  for (int k = tid; k < Kp; k += blockDim.x) koff[k] = koffset(k, K);
+  for (int i = tid; i < NP * KH; i += blockDim.x) {
+    const int n = i / KH, kk = 2 * (i - n * KH);
+    const float v0 = (n < CO && kk < K) ? wval(w[(int64_t)n * K + kk]) : 0.0f;
+    const float v1 = (n < CO && kk + 1 < K) ? wval(w[(int64_t)n * K + kk + 1]) : 0.0f;
+    if (TERMS == 3) split2(v0, v1, bh[i], bl[i]);
+    else bh[i] = pack(v0, v1);
+  }
+  __syncthreads();
+  float acc[2][NT][4];
 #pragma unroll
-  for (int o = 0; o < CO; ++o) acc[o] = bias ? bias[o] : 0.0f;
-  for (int c0 = 0; c0 < Cin; c0 += CI_CHUNK) {
-    const int cn = min(CI_CHUNK, Cin - c0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cn * (TS + 2) * (TS + 2); i += blockDim.x) {
-      const int c = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
-      const int yy = y0 + r / (TS + 2) - 1, xx = x0 + r % (TS + 2) - 1;
-      sin_[c][r / (TS + 2)][r % (TS + 2)] =
-          (yy >= 0 && yy < H && xx >= 0 && xx < W) ? inb[((int64_t)(c0 + c) * H + yy) * W + xx] : 0.0f;
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.0f;
+  const int r0 = 2 * wid;
+  for (int k0 = 0; k0 < Kp; k0 += 16) {
+    const int ka = k0 + 2 * tq, kb = ka + 8;
+    const int oa0 = koff[ka], oa1 = koff[ka + 1], ob0 = koff[kb], ob1 = koff[kb + 1];
+    uint32_t wh[NT][2], wl[NT][2];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      wh[nt][0] = bh[(nt * 8 + g) * KH + ka / 2];
+      wh[nt][1] = bh[(nt * 8 + g) * KH + kb / 2];
+      if (TERMS == 3) {
+        wl[nt][0] = bl[(nt * 8 + g) * KH + ka / 2];
+        wl[nt][1] = bl[(nt * 8 + g) * KH + kb / 2];
+      }
     }
-    for (int i = threadIdx.x; i < cn * 9 * CO; i += blockDim.x) {
-      const int c = i / (9 * CO), r = i % (9 * CO), t = r / CO, o = r % CO;
-      sw[c][t][o] = wval(w[((int64_t)o * Cin + (c0 + c)) * 9 + t]);
-    }
-    __syncthreads();
-    for (int c = 0; c < cn; ++c) {
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const float v = sin_[c][ty + t / 3][tx + t % 3];
+    for (int mt = 0; mt < 2; ++mt) {
+      const int base = (r0 + mt) * (TS + 2) + g;  // pixel (row r0 + mt, column g); + 8 for column g + 8
+      const float e0 = sh[oa0 + base], e1 = sh[oa1 + base], e2 = sh[oa0 + base + 8], e3 = sh[oa1 + base + 8];
+      const float e4 = sh[ob0 + base], e5 = sh[ob1 + base], e6 = sh[ob0 + base + 8], e7 = sh[ob1 + base + 8];
+      uint32_t ah[4], al[4];
+      if (TERMS == 3) {
+        split2(e0, e1, ah[0], al[0]);
+        split2(e2, e3, ah[1], al[1]);
+        split2(e4, e5, ah[2], al[2]);
+        split2(e6, e7, ah[3], al[3]);
+      } else {
+        ah[0] = pack(e0, e1);
+        ah[1] = pack(e2, e3);
+        ah[2] = pack(e4, e5);
+        ah[3] = pack(e6, e7);
+      }
 #pragma unroll
-        for (int o = 0; o < CO; ++o) acc[o] += v * sw[c][t][o];
+      for (int nt = 0; nt < NT; ++nt) {
+        mma16816(acc[mt][nt], ah, wh[nt]);
+        if (TERMS == 3) {
+          mma16816(acc[mt][nt], ah, wl[nt]);
+          mma16816(acc[mt][nt], al, wh[nt]);
+        }
       }
     }
   }
-  float* ob = out + (int64_t)bimg * CO * H * W;
-  const int y = y0 + ty, x = x0 + tx;
+  float* ob = out + (int64_t)img * CO * H * W;
 #pragma unroll
-  for (int o = 0; o < CO; ++o) {
-    float v = acc[o];
-    if (relu) v = fmaxf(v, 0.0f);
-    ob[((int64_t)o * H + y) * W + x] = v;
-  }
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = nt * 8 + 2 * tq + (q & 1), px = g + ((q & 2) ? 8 : 0);
+        if (o >= CO) continue;
+        float v = acc[mt][nt][q] + (bias ? bias[o] : 0.0f);
+        if (relu) v = fmaxf(v, 0.0f);
+        ob[((int64_t)o * H + y0 + r0 + mt) * W + x0 + px] = v;
+      }
 }
 
 // wflip[c][o][t] = w[o][c][8 - t]: the input gradient is the convolution of the
@@ -106,63 +202,104 @@ __global__ void k_relu_mask(float* __restrict__ g, const float* __restrict__ act
 }
 
 // weight-gradient partials of one band of 16 rows of one image:
-// part[band][o][c][t] = sum_{pixels} g[o][y][x] in[c][y+dy-1][x+dx-1].
-// All input channels and output gradients of a 16 x 16 tile are staged in shared
-// memory; thread (c, og) owns c_out 4og..4og+3 and all 9 taps (Cin * ceil(Cout/4)
-// <= 256 threads).
-__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ in, int Cin, const float* __restrict__ g,
-                                               int Cout, int H, int W, float* __restrict__ part) {
-  extern __shared__ __align__(16) float smw[];
-  float* sin_ = smw;                             // [Cin][18][18]
-  float* sg = smw + Cin * (TS + 2) * (TS + 2);   // [Cout][256]
-  const int band = blockIdx.x, bimg = blockIdx.y;
-  const int nog = (Cout + 3) / 4;
-  const float* inb = in + (int64_t)bimg * Cin * H * W;
-  const float* gb = g + (int64_t)bimg * Cout * H * W;
-  const int y0 = band * TS;
-  float* pout = part + ((int64_t)bimg * gridDim.x + band) * (int64_t)Cout * Cin * 9;
-  const int pc = threadIdx.x / nog, og = threadIdx.x % nog;
-  const bool active = threadIdx.x < Cin * nog;
-  float acc[4][9];
+// part[band][o][c][t] = sum_{pixels} g[o][y][x] in[c][y+dy-1][x+dx-1], a GEMM with
+// M = c_out, N = c_in x tap, K = the band's pixels (16 per MMA step: one row of a
+// 16 x 16 tile), 3xBF16.  9 warps; warp w takes the n8 tiles w, w + 9, w + 18, w + 27.
+constexpr int WG_WARPS = 9;
+inline size_t wgrad_smem(int Cin, int Cout) {
+  const int MP = Cout <= 16 ? 16 : 32, NP = (Cin * 9 + 7) / 8 * 8;
+  return (size_t)(Cin * tcc::HALO + 4) * sizeof(float) + (size_t)NP * sizeof(int) +
+         (size_t)MP * (TS * TS / 2) * sizeof(uint32_t) * 2;
+}
+__global__ void __launch_bounds__(WG_WARPS * 32) k_wgrad_tc(const float* __restrict__ in, int Cin,
+                                                            const float* __restrict__ g, int Cout, int H, int W,
+                                                            float* __restrict__ part) {
+  using namespace tcc;
+  extern __shared__ __align__(16) unsigned char smc[];
+  const int K = Cin * 9, NT = (K + 7) / 8, NP = NT * 8, MT = Cout <= 16 ? 1 : 2, MP = 16 * MT;
+  constexpr int PH = TS * TS / 2;                   // pixel pairs of a tile
+  float* sh = reinterpret_cast<float*>(smc);        // [Cin][18][18] (+4 floats of alignment)
+  int* noff = reinterpret_cast<int*>(sh + Cin * HALO + 4);
+  uint32_t* gh = reinterpret_cast<uint32_t*>(noff + NP);  // [MP][PH] gradient pairs, hi
+  uint32_t* gl = gh + MP * PH;                            // lo
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+  const int band = blockIdx.x, img = blockIdx.y, y0 = band * TS;
+  const float* inb = in + (int64_t)img * Cin * H * W;
+  const float* gb = g + (int64_t)img * Cout * H * W;
+  for (int n = tid; n < NP; n += blockDim.x) noff[n] = koffset(n, K);
+  float acc[2][4][4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[q][t] = 0.0f;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][j][q] = 0.0f;
   for (int x0 = 0; x0 < W; x0 += TS) {
     __syncthreads();
-    for (int i = threadIdx.x; i < Cin * (TS + 2) * (TS + 2); i += blockDim.x) {
-      const int c = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
+    for (int i = tid; i < Cin * HALO; i += blockDim.x) {
+      const int c = i / HALO, r = i - c * HALO;
       const int yy = y0 + r / (TS + 2) - 1, xx = x0 + r % (TS + 2) - 1;
-      sin_[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? inb[((int64_t)c * H + yy) * W + xx] : 0.0f;
+      sh[i] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? inb[((int64_t)c * H + yy) * W + xx] : 0.0f;
     }
-    for (int i = threadIdx.x; i < Cout * TS * TS; i += blockDim.x) {
-      const int o = i / (TS * TS), p = i % (TS * TS);
-      sg[i] = gb[((int64_t)o * H + y0 + p / TS) * W + x0 + p % TS];
+    for (int i = tid; i < MP * PH; i += blockDim.x) {
+      const int o = i / PH, pp = i - o * PH, p = 2 * pp;
+      float v0 = 0.0f, v1 = 0.0f;
+      if (o < Cout) {
+        const float* row = gb + ((int64_t)o * H + y0 + p / TS) * W + x0 + p % TS;
+        v0 = row[0];
+        v1 = row[1];
+      }
+      split2(v0, v1, gh[i], gl[i]);
     }
     __syncthreads();
-    if (active) {
-      const float* sc = sin_ + pc * (TS + 2) * (TS + 2);
-      for (int p = 0; p < TS * TS; ++p) {
-        const int py = p / TS, px = p % TS;
-        float v[9];
+    for (int r = 0; r < TS; ++r) {  // K step: the 16 pixels of tile row r
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) v[t] = sc[(py + t / 3) * (TS + 2) + px + t % 3];
+      for (int mt = 0; mt < 2; ++mt) {
+        if (mt >= MT) break;
+        const int o = mt * 16 + gq, pa = (r * TS + 2 * tq) / 2, pb = pa + 4;
+        ah[mt][0] = gh[o * PH + pa];
+        al[mt][0] = gl[o * PH + pa];
+        ah[mt][1] = gh[(o + 8) * PH + pa];
+        al[mt][1] = gl[(o + 8) * PH + pa];
+        ah[mt][2] = gh[o * PH + pb];
+        al[mt][2] = gl[o * PH + pb];
+        ah[mt][3] = gh[(o + 8) * PH + pb];
+        al[mt][3] = gl[(o + 8) * PH + pb];
+      }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int o = 4 * og + q;
-          const float gv = (o < Cout) ? sg[o * TS * TS + p] : 0.0f;
+      for (int j = 0; j < 4; ++j) {
+        const int nt = wid + WG_WARPS * j;
+        if (nt >= NT) break;
+        const int off = noff[nt * 8 + gq] + r * (TS + 2) + 2 * tq;  // pixels 2 tq, 2 tq + 1 (+ 8) of row r
+        uint32_t bh[2], bl[2];
+        split2(sh[off], sh[off + 1], bh[0], bl[0]);
+        split2(sh[off + 8], sh[off + 9], bh[1], bl[1]);
 #pragma unroll
-          for (int t = 0; t < 9; ++t) acc[q][t] += gv * v[t];
+        for (int mt = 0; mt < 2; ++mt) {
+          if (mt >= MT) break;
+          mma16816(acc[mt][j], ah[mt], bh);
+          mma16816(acc[mt][j], ah[mt], bl);
+          mma16816(acc[mt][j], al[mt], bh);
         }
       }
     }
   }
-  if (active)
-    for (int q = 0; q < 4; ++q) {
-      const int o = 4 * og + q;
-      if (o < Cout)
-        for (int t = 0; t < 9; ++t) pout[((int64_t)o * Cin + pc) * 9 + t] = acc[q][t];
+  float* pout = part + ((int64_t)img * gridDim.x + band) * (int64_t)Cout * K;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    if (mt >= MT) break;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nt = wid + WG_WARPS * j;
+      if (nt >= NT) break;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int o = mt * 16 + gq + ((q & 2) ? 8 : 0), n = nt * 8 + 2 * tq + (q & 1);
+        if (o < Cout && n < K) pout[(int64_t)o * K + n] = acc[mt][j][q];
+      }
     }
+  }
 }
 
 // gw[i] = sum over partials (fixed order)
@@ -250,29 +387,35 @@ __global__ void k_init(float* __restrict__ w, int64_t n, int64_t off, int fan_in
 
 inline int blocks(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
+// bfloat16 weights (inference): one bfloat16 product; float32 weights (training,
+// gradients): the three-term split
+template <typename WT> constexpr int conv_terms() { return std::is_same<WT, __nv_bfloat16>::value ? 1 : 3; }
+
+template <int CO, typename WT>
+gs_status conv_launch(const float* in, int Cin, const WT* w, const float* bias, float* out, int B, int H, int W,
+                      int relu, cudaStream_t st) {
+  constexpr int TERMS = conv_terms<WT>();
+  const size_t sh = conv_smem<WT>(Cin, CO, TERMS);
+  if (sh > 48 * 1024)
+    GS_CUDA(cudaFuncSetAttribute((const void*)k_conv3_tc<CO, TERMS, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sh));
+  dim3 grid(W / TS, H / TS, B);
+  GS_LAUNCH("cnn_conv3", st, k_conv3_tc<CO, TERMS, WT><<<grid, 256, sh, st>>>(in, Cin, w, bias, out, H, W, relu));
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
 template <typename WT>
 gs_status conv(const float* in, int Cin, const WT* w, const float* bias, float* out, int Cout, int B, int H, int W,
                int relu, cudaStream_t st) {
-  dim3 grid(W / TS, H / TS, B);
   switch (Cout) {
-    case 2:
-      GS_LAUNCH("cnn_conv3", st, k_conv3<2, WT><<<grid, 256, 0, st>>>(in, Cin, w, bias, out, H, W, relu));
-      break;
-    case 8:
-      GS_LAUNCH("cnn_conv3", st, k_conv3<8, WT><<<grid, 256, 0, st>>>(in, Cin, w, bias, out, H, W, relu));
-      break;
-    case 16:
-      GS_LAUNCH("cnn_conv3", st, k_conv3<16, WT><<<grid, 256, 0, st>>>(in, Cin, w, bias, out, H, W, relu));
-      break;
-    case 32:
-      GS_LAUNCH("cnn_conv3", st, k_conv3<32, WT><<<grid, 256, 0, st>>>(in, Cin, w, bias, out, H, W, relu));
-      break;
-    default:
-      set_error("convolution with %d output channels has no compiled kernel (2, 8, 16, 32)", Cout);
-      return GS_EUNSUPPORTED;
+    case 2: return conv_launch<2, WT>(in, Cin, w, bias, out, B, H, W, relu, st);
+    case 8: return conv_launch<8, WT>(in, Cin, w, bias, out, B, H, W, relu, st);
+    case 16: return conv_launch<16, WT>(in, Cin, w, bias, out, B, H, W, relu, st);
+    case 32: return conv_launch<32, WT>(in, Cin, w, bias, out, B, H, W, relu, st);
   }
-  GS_CUDA(cudaGetLastError());
-  return GS_OK;
+  set_error("convolution with %d output channels has no compiled kernel (2, 8, 16, 32)", Cout);
+  return GS_EUNSUPPORTED;
 }
 
 template <typename T>
@@ -309,9 +452,11 @@ gs_status backward(gs_cnn_s* N, const float* u, const float* tgt, int B, double*
     if (l < N->L - 1) GS_LAUNCH("cnn_relu_mask", st, k_relu_mask<<<blocks(B * Co * HW), 256, 0, st>>>(g, N->act[l + 1], (int64_t)B * Co * HW));
     const int nbands = N->H / TS;
     const int64_t nwl = (int64_t)Co * Ci * 9;
-    const size_t shw = ((size_t)Ci * (TS + 2) * (TS + 2) + (size_t)Co * TS * TS) * sizeof(float);
-    if (shw > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shw));
-    GS_LAUNCH("cnn_wgrad", st, k_wgrad<<<dim3(nbands, B), 256, shw, st>>>(N->act[l], Ci, g, Co, N->H, N->W, N->part));
+    const size_t shw = wgrad_smem(Ci, Co);
+    if (shw > 48 * 1024)
+      GS_CUDA(cudaFuncSetAttribute((const void*)k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shw));
+    GS_LAUNCH("cnn_wgrad", st, k_wgrad_tc<<<dim3(nbands, B), WG_WARPS * 32, shw, st>>>(N->act[l], Ci, g, Co, N->H, N->W,
+                                                                                      N->part));
     GS_LAUNCH("cnn_wgrad_sum", st, k_sum_parts<<<blocks(nwl), 256, 0, st>>>(N->part, nbands * B, nwl, N->gw + N->woff[l]));
     GS_LAUNCH("cnn_bgrad", st, k_bgrad<<<Co, 256, 0, st>>>(g, B, Co, HW, N->gb + N->boff[l]));
     if (l > 0) {
