@@ -83,13 +83,13 @@ static void free_graphs(PrecData<R>& D) {
 }
 
 static void free_prec_f(PrecData<float>& D) {
-  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner, D.hs, D.hp,
+  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner, D.hs, D.hp, D.lat,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);
 }
 static void free_prec_d(PrecData<double>& D) {
-  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner, D.hs, D.hp,
+  void* ps[] = {D.frac, D.win, D.w, D.bf, D.deap, D.tw, D.grid, D.hbuf, D.ftmp, D.side, D.part, D.corner, D.hs, D.hp, D.lat,
                 D.vx, D.vs, D.vp, D.vr, D.vq, D.vz};
   for (void* p : ps)
     if (p) cudaFree(p);

@@ -99,6 +99,7 @@ struct PrecData {
   C<R>* corner = nullptr; // 2D: (2b)^2 corner adjoint, 1D: 2b boundary adjoint
   C<R>* hs = nullptr;     // 2D float32: N x n, x transforms of the rows of s (CGNR)
   C<R>* hp = nullptr;     // 2D float32: N x n, x transforms of the rows of p (CGNR)
+  C<R>* lat = nullptr;    // 2D lattice plans: per-bin side-line partials [bin][2][2b][tile]
   int64_t part_stride = 0;
   // solver vectors (sorted order for M-vectors)
   C<R>* vx = nullptr;  // ncoef

@@ -161,56 +161,61 @@ __global__ void k_fold2d_grid(const int32_t* __restrict__ bin_start, int tile, i
   grid[(int64_t)jx * n + jy] = acc;
 }
 
-// side lines: dim 0 (x-sides along y), CTA per row of bins by, thread (k, jy - by
-// tile); dim 1 (y-sides along x), CTA per column of bins bx, thread (k, jx - bx
-// tile), samples of that column through its work items.  Value per sample:
-// dim 0: u conj(wy) conj(bx_k) at jy; dim 1: u conj(wx) conj(by_k) at jx.
+// side lines, step 1: CTA per bin (bx, by), thread (dim, k, l): the bin's share of
+// dim 0 (x-sides along y): u conj(wy) conj(bx_k) of its samples at jy = by tile + l;
+// dim 1 (y-sides along x): u conj(wx) conj(by_k) of its samples at jx = bx tile + l
 template <typename R>
-__global__ void k_fold2d_side(int dim, const int32_t* __restrict__ bin_start, const int32_t* __restrict__ work,
-                              const int32_t* __restrict__ wcol, const int32_t* __restrict__ wcol_start, int tile,
-                              int nbx, const int32_t* __restrict__ fl, const C<R>* __restrict__ w,
-                              const C<R>* __restrict__ bf, int b2, const C<R>* __restrict__ u,
-                              const int32_t* __restrict__ perm, int64_t M, int n, C<R>* __restrict__ side) {
+__global__ void k_fold2d_side_part(const int32_t* __restrict__ bin_start, int tile, int nbx,
+                                   const int32_t* __restrict__ fl, const C<R>* __restrict__ w,
+                                   const C<R>* __restrict__ bf, int b2, const C<R>* __restrict__ u,
+                                   const int32_t* __restrict__ perm, int64_t M, C<R>* __restrict__ lat) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  int* pos = reinterpret_cast<int*>(smraw);                               // [FOLD_CHUNK]
-  C<R>* uw = reinterpret_cast<C<R>*>(smraw + FOLD_CHUNK * sizeof(C<R>));  // [FOLD_CHUNK]
-  C<R>* fk = uw + FOLD_CHUNK;                                             // [FOLD_CHUNK][b2]
-  const int line = blockIdx.x;  // by (dim 0) or bx (dim 1)
-  const int t = threadIdx.x, k = t / tile, jl = t - k * tile;
-  const bool active = k < b2;
-  const int od = 1 - dim;  // the other dimension's factors and coordinates
+  int* pos = reinterpret_cast<int*>(smraw);                               // [FOLD_CHUNK][2]
+  C<R>* uw = reinterpret_cast<C<R>*>(smraw + 2 * FOLD_CHUNK * sizeof(C<R>));  // [FOLD_CHUNK][2]
+  C<R>* fk = uw + 2 * FOLD_CHUNK;                                         // [FOLD_CHUNK][2][b2]
+  const int bin = blockIdx.x, bx = bin % nbx, by = bin / nbx;
+  const int t = threadIdx.x, dim = t / (b2 * tile), r = t - dim * b2 * tile, k = r / tile, l = r - k * tile;
+  const bool active = dim < 2;
+  const int s0 = bin_start[bin], s1 = bin_start[bin + 1];
   C<R> acc = mk<R>(0, 0);
-  // the line's sample ranges: one contiguous range (dim 0) or the column's work items (dim 1)
-  const int nr = (dim == 0) ? 1 : wcol_start[line + 1] - wcol_start[line];
-  for (int r = 0; r < nr; ++r) {
-    int s0, s1;
-    if (dim == 0) {
-      s0 = bin_start[line * nbx];
-      s1 = bin_start[(line + 1) * nbx];
-    } else {
-      const int wi = wcol[wcol_start[line] + r];
-      s0 = work[3 * wi + 1];
-      s1 = work[3 * wi + 2];
+  for (int c0 = s0; c0 < s1; c0 += FOLD_CHUNK) {
+    const int nc = min(FOLD_CHUNK, s1 - c0);
+    __syncthreads();
+    for (int i = t; i < nc; i += blockDim.x) {
+      const int s = c0 + i;
+      const C<R> us = u[perm ? perm[s] : s];
+      pos[2 * i] = fl[M + s] - by * tile;  // dim 0: position along y
+      pos[2 * i + 1] = fl[s] - bx * tile;  // dim 1: position along x
+      uw[2 * i] = cmulc(us, w[M + s]);
+      uw[2 * i + 1] = cmulc(us, w[s]);
     }
-    for (int c0 = s0; c0 < s1; c0 += FOLD_CHUNK) {
-      const int nc = min(FOLD_CHUNK, s1 - c0);
-      __syncthreads();
-      for (int i = t; i < nc; i += blockDim.x) {
-        const int s = c0 + i;
-        pos[i] = fl[(int64_t)od * M + s] - line * tile;
-        uw[i] = cmulc(u[perm ? perm[s] : s], w[(int64_t)od * M + s]);
-      }
-      for (int i = t; i < nc * b2; i += blockDim.x) {
-        const int q = i / b2, kk = i - q * b2;
-        fk[i] = bf[((int64_t)dim * M + c0 + q) * b2 + kk];
-      }
-      __syncthreads();
-      if (active)
-        for (int i = 0; i < nc; ++i)
-          if (pos[i] == jl) acc = cadd(acc, cmulc(uw[i], fk[i * b2 + k]));
+    for (int i = t; i < nc * 2 * b2; i += blockDim.x) {
+      const int q = i / (2 * b2), rr = i - q * 2 * b2, d = rr / b2, kk = rr - d * b2;
+      fk[i] = bf[((int64_t)d * M + c0 + q) * b2 + kk];  // d = 0: bx, d = 1: by
     }
+    __syncthreads();
+    if (active)
+      for (int i = 0; i < nc; ++i)
+        if (pos[2 * i + dim] == l) acc = cadd(acc, cmulc(uw[2 * i + dim], fk[(i * 2 + dim) * b2 + k]));
   }
-  if (active) side[((int64_t)dim * b2 + k) * n + line * tile + jl] = acc;
+  if (active) lat[(((int64_t)bin * 2 + dim) * b2 + k) * tile + l] = acc;
+}
+
+// side lines, step 2: thread (dim, k, j): the bins' shares summed in bin order,
+// over bx (dim 0, j = jy) or over by (dim 1, j = jx)
+template <typename R>
+__global__ void k_fold2d_side_sum(const C<R>* __restrict__ lat, int tile, int nbx, int b2, int n,
+                                  C<R>* __restrict__ side) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)2 * b2 * n) return;
+  const int dim = (int)(t / ((int64_t)b2 * n)), r = (int)(t - (int64_t)dim * b2 * n), k = r / n, j = r - k * n;
+  const int jb = j / tile, l = j - jb * tile;
+  C<R> acc = mk<R>(0, 0);
+  for (int q = 0; q < nbx; ++q) {
+    const int bin = (dim == 0) ? q + nbx * jb : jb + nbx * q;
+    acc = cadd(acc, lat[(((int64_t)bin * 2 + dim) * b2 + k) * tile + l]);
+  }
+  side[((int64_t)dim * b2 + k) * n + j] = acc;
 }
 
 }  // namespace
@@ -248,15 +253,17 @@ gs_status lattice_fold(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t* pe
               k_fold2d_grid<R><<<P->nbins, tile * tile, 0, st>>>(P->bin_start, tile, P->nbx, P->fl, D.w, u, perm, M,
                                                                   n, D.grid));
     if (b2 > 0) {
-      const size_t sh = (size_t)FOLD_CHUNK * (sizeof(C<R>) + sizeof(C<R>) + (size_t)b2 * sizeof(C<R>));
+      const size_t sh = (size_t)FOLD_CHUNK * 2 * (2 + b2) * sizeof(C<R>);
       if (sh > 48 * 1024)
-        GS_CUDA(cudaFuncSetAttribute((const void*)k_fold2d_side<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sh));
-      const int thr = ((b2 * tile + 31) / 32) * 32;
-      for (int dim = 0; dim < 2; ++dim)
-        GS_LAUNCH(pname<R>("fold2d_side<f32>", "fold2d_side<f64>"), st,
-                  k_fold2d_side<R><<<P->nbx, thr, sh, st>>>(dim, P->bin_start, P->work, P->wcol, P->wcol_start, tile,
-                                                            P->nbx, P->fl, D.w, D.bf, b2, u, perm, M, n, D.side));
+        GS_CUDA(cudaFuncSetAttribute((const void*)k_fold2d_side_part<R>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      const int thr = ((2 * b2 * tile + 31) / 32) * 32;
+      GS_LAUNCH(pname<R>("fold2d_side<f32>", "fold2d_side<f64>"), st,
+                k_fold2d_side_part<R><<<P->nbins, thr, sh, st>>>(P->bin_start, tile, P->nbx, P->fl, D.w, D.bf, b2, u,
+                                                                 perm, M, D.lat));
+      const int64_t tot = (int64_t)2 * b2 * n;
+      GS_LAUNCH(pname<R>("fold2d_side<f32>", "fold2d_side<f64>"), st,
+                k_fold2d_side_sum<R><<<(tot + 255) / 256, 256, 0, st>>>(D.lat, tile, P->nbx, b2, n, D.side));
       GS_LAUNCH(pname<R>("fold_chan<f32>", "fold_chan<f64>"), st,
                 k_fold_chan<R><<<b2 * b2, 256, 0, st>>>(D.bf, b2, 2, u, perm, M, D.corner));
     }

@@ -361,6 +361,8 @@ gs_status alloc_prec(Plan* P, PrecData<R>& D, int m) {
       GS_TRY(dalloc(&D.side, (size_t)2 * (b2 > 0 ? b2 : 1) * n));
       GS_TRY(dalloc(&D.hs, (size_t)N * n));
       GS_TRY(dalloc(&D.hp, (size_t)N * n));
+      if (P->lattice && b2 > 0)
+        GS_TRY(dalloc(&D.lat, (size_t)P->nbins * 2 * b2 * P->tile));
       int pw = TILE2 + 2 * m;
       D.part_stride = (int64_t)pw * pw + 2 * b2 * pw + b2 * b2;
     }
