@@ -5,8 +5,9 @@ they run (code recording a CUDA graph, runtimes with a fixed device-memory
 arena): it computes the same T^H y with the spread scratch in a fixed static
 device array.  Here its output, through the C ABI, must equal the regular
 entry point's on two calls in a row (the array keeps the previous call's
-contents), in float64 and float32, for a 1D and a 2D plan; a plan whose scratch
-exceeds the fixed array is rejected.
+contents), in float64 and float32, for two 1D plans (one large enough for the
+two-pass FFT, n = 8192) and a 2D plan; a plan whose scratch exceeds the fixed
+array is rejected.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process.
@@ -31,7 +32,9 @@ def _plans():
     p1 = gs.Plan.plan_1d(xi1, 4, 9, bandwidth=1024.0, direct=0)
     xi2 = g.uniform(-48, 48, size=(3001, 2))
     p2 = gs.Plan.plan_2d(xi2, 4, 5, direct=0)
-    return [p1, p2]
+    xi3 = g.uniform(-4096, 4096, 12001)  # J = 12: n = 8192, the four-step FFT
+    p3 = gs.Plan.plan_1d(xi3, 4, 12, bandwidth=4096.0, direct=0)
+    return [p1, p2, p3]
 
 
 @pytest.mark.parametrize("prec", [gs.GS_FP64, gs.GS_FP32])
