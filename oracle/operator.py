@@ -44,21 +44,26 @@ class Basis1D:
             return phihat_haar_closed(eta)
         return phihat(eta, self.k, self.h)
 
-    def factors(self, xi) -> np.ndarray:
-        """t[m, i]: entry of T (without density weight) for samples xi, all N columns."""
+    def factors(self, xi, cols=None) -> np.ndarray:
+        """t[m, i]: entry of T (without density weight) for samples xi, all N columns,
+        or only the columns listed in cols (in that order)."""
         xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
         N, J, b = self.N, self.J, self.b
+        cols = np.arange(N) if cols is None else np.asarray(cols, dtype=np.int64)
         s = 2.0 ** (-J / 2.0)
         eta = xi / 2.0**J
-        t = np.zeros((xi.size, N), dtype=np.complex128)
-        kk = np.arange(b, N - b) - N // 2
-        t[:, b:N - b] = s * np.exp(-2j * np.pi * np.outer(eta, kk)) * self.phihat(eta)[:, None]
+        t = np.zeros((xi.size, cols.size), dtype=np.complex128)
+        inner = (cols >= b) & (cols < N - b)
+        kk = cols[inner] - N // 2
+        t[:, inner] = s * np.exp(-2j * np.pi * np.outer(eta, kk)) * self.phihat(eta)[:, None]
         if b:
             vL = self.left.ft(eta)  # (p, M)
             vR = self.right.ft(eta)
-            for i in range(b):
-                t[:, i] = s * np.exp(1j * np.pi * xi) * vL[i]
-                t[:, N - 1 - i] = s * np.exp(-1j * np.pi * xi) * vR[i]
+            for j, i in enumerate(cols):
+                if i < b:
+                    t[:, j] = s * np.exp(1j * np.pi * xi) * vL[i]
+                elif i >= N - b:
+                    t[:, j] = s * np.exp(-1j * np.pi * xi) * vR[N - 1 - i]
         return t
 
 

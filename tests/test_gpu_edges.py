@@ -1,8 +1,9 @@
 """GPU edge cases against the oracle: a single sample (1D and 2D, NFFT path with
 one work item holding one sample), the largest 2D grid (J = 9, n = 1024) and the
 largest 1D grid (J = 19, n = 2^20, the four-step FFT at n1 = n2 = 1024).  The
-large cases compare T x on sampled rows the oracle evaluates one by one and
-check T^H through the adjoint identity."""
+large cases compare T x on sampled rows the oracle evaluates one by one, check
+the adjoint identity, and (1D) compare T^H on sampled coefficients (the 2D
+J = 9 grid's T^H is compared through golden files, tests/test_gpu_golden.py)."""
 import numpy as np
 import pytest
 
@@ -86,7 +87,16 @@ def test_largest_1d_grid(prec):
     plan = gs.Plan.plan_1d(xi, 4, J, direct=0)
     x = rand_c(g, N)
     idx = np.sort(g.choice(M, size=16, replace=False))
-    rows = Basis1D(4, J).factors(xi[idx]) @ x
+    B = Basis1D(4, J)
+    rows = B.factors(xi[idx]) @ x
     y = plan.T(dev(x, prec), prec).cpu().numpy()
     assert rel(y[idx], rows) < tol_for(prec, 2 * N)
     assert adjoint_gap(plan, prec, g) < (1e-12 if prec == gs.GS_FP64 else 1e-5)
+    # T^H element by element on the boundary coefficients and 56 sampled interior ones
+    u = rand_c(g, M)
+    cols = np.r_[0:4, N - 4:N, np.sort(g.choice(np.arange(4, N - 4), 56, replace=False))]
+    zref = np.zeros(cols.size, dtype=complex)
+    for s in range(0, M, 20000):
+        zref += B.factors(xi[s:s + 20000], cols).conj().T @ u[s:s + 20000]
+    z = plan.TH(dev(u, prec), prec).cpu().numpy()
+    assert rel(z[cols], zref) < tol_for(prec, 2 * N)

@@ -370,3 +370,13 @@ def test_voronoi_2d_regular_grid():
     X, Y = np.meshgrid(k, k)
     mu, delta = voronoi_2d(np.stack([X.ravel(), Y.ravel()], axis=1), 3.5)
     assert np.allclose(mu, 1.0, rtol=0, atol=1e-13) and abs(delta - np.sqrt(0.5)) < 1e-13
+
+
+@pytest.mark.parametrize("p", [1, 4])
+def test_factor_columns_subset_equals_full_rows(p):
+    # the column-subset form of the factor rows (used for sampled T^H at sizes where
+    # the full rows do not fit) takes the same entries as the full rows
+    B = Basis1D(p, 6)
+    xi = np.random.default_rng(41).uniform(-150, 150, 40)
+    cols = np.array([0, 3, 5, 31, 32, 58, 60, 63])
+    assert np.array_equal(B.factors(xi, cols), B.factors(xi)[:, cols])
