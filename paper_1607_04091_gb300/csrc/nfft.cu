@@ -193,6 +193,29 @@ __device__ inline void batched(int total, L load, S store) {
   }
 }
 
+// The n/2 twiddles of a 2D pass into shared memory: fetched into registers
+// before the pass issues its row or column loads and stored after them, so that
+// both share one round trip; the radix passes then read their twiddles from
+// shared memory instead of waiting on a global load before each barrier.
+template <typename R> struct TwStage {
+  C<R> v[4];
+  __device__ inline void fetch(const C<R>* __restrict__ tw, int nh) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < nh) v[u] = tw[i];
+    }
+  }
+  __device__ inline void store(const C<R>* __restrict__ tw, C<R>* tws, int nh) const {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = threadIdx.x + u * blockDim.x;
+      if (i < nh) tws[i] = v[u];
+    }
+    for (int i = threadIdx.x + 4 * blockDim.x; i < nh; i += blockDim.x) tws[i] = tw[i];
+  }
+};
+
 // ---------------------------------------------------------------- 1D forward
 // deapodise + zero-pad + FFT: one CTA, n <= 16384 (float) / 8192 (double)
 template <typename R>
@@ -442,8 +465,11 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
                               int logn, int rows, const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  C<R>* tws = buf + (size_t)rows * n;
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
+  TwStage<R> tp;
+  tp.fetch(tw, n / 2);
   // grid point l of row r holds coefficient i = l + N/2 (mod n), deapodised, or 0
   batched<PPT_ROW, C<R>>(
       nr * n,
@@ -458,8 +484,9 @@ __global__ void k_fwd2d_pass1(const C<R>* __restrict__ x, const R* __restrict__ 
         return v;
       },
       [&](int t, C<R> v) { buf[t] = v; });
+  tp.store(tw, tws, n / 2);
   __syncthreads();
-  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, false);
+  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tws, false);
   for (int t = threadIdx.x; t < nr * n; t += blockDim.x) hbuf[(int64_t)j0 * n + t] = buf[t];
 }
 
@@ -472,9 +499,12 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
                               PComb<R> pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  C<R>* tws = buf + (size_t)cols * n;
   const int c0 = blockIdx.x * cols;
   const int ntot = n + 2 * b;
   const int nc = min(cols, ntot - c0);
+  TwStage<R> tp;
+  tp.fetch(tw, n / 2);
   // CG direction update (PComb): every row j < N of each column is visited once
   // below, the x-boundary rows (deap = 0) included, so that hp and the boundary
   // columns of p are complete for the interpolation
@@ -525,8 +555,9 @@ __global__ void k_fwd2d_pass2(const C<R>* __restrict__ hbuf, const C<R>* __restr
         return v;
       },
       [&](int t, C<R> v) { buf[t] = v; });
+  tp.store(tw, tws, n / 2);
   __syncthreads();
-  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tw, false);
+  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tws, false);
   for (int t = threadIdx.x; t < nc * n; t += blockDim.x) {
     int c = t / n, l = t - c * n;
     int col = c0 + c;
@@ -708,9 +739,12 @@ __global__ void k_adj2d_pass2(const C<R>* __restrict__ grid, const C<R>* __restr
                               const C<R>* __restrict__ tw, C<R>* __restrict__ hbuf, C<R>* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  C<R>* tws = buf + (size_t)cols * n;
   const int c0 = blockIdx.x * cols;
   const int ntot = n + 2 * b;
   const int nc = min(cols, ntot - c0);
+  TwStage<R> tp;
+  tp.fetch(tw, n / 2);
   batched<PPT_ROW, C<R>>(
       nc * n,
       [&](int t) {
@@ -718,8 +752,9 @@ __global__ void k_adj2d_pass2(const C<R>* __restrict__ grid, const C<R>* __restr
         return (col < n) ? grid[(int64_t)col * n + l] : side[(int64_t)(col - n) * n + l];
       },
       [&](int t, C<R> v) { buf[t] = v; });
+  tp.store(tw, tws, n / 2);
   __syncthreads();
-  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tw, true);
+  fft_smem<R, PPT_ROW>(buf, nc, n, logn, tws, true);
   // t = c + nc j: column c of row j, so that consecutive threads write neighbouring columns
   batched<PPT_ROW, Cv<R>>(
       nc * N,
@@ -749,9 +784,62 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
                               C<R>* __restrict__ z, CgStep<R> cg) {
   extern __shared__ __align__(16) unsigned char smraw[];
   C<R>* buf = reinterpret_cast<C<R>*>(smraw);
+  C<R>* tws = buf + (size_t)rows * n;
   const int j0 = blockIdx.x * rows;
   const int nr = min(rows, N - j0);
   const int b2 = 2 * b;
+  const int cnt = nr * N;  // entries t = r N + i of these rows
+  // entry t of z: from the inverse transform (interior i), a corner (boundary i
+  // and j), or not written here (boundary i, interior j: pass 2 wrote it)
+  auto zval = [&](int t, R dv) -> Cv<R> {
+    const int r = t / N, i = t - r * N, j = j0 + r;
+    if (dv != (R)0) return Cv<R>{cscale(buf[r * n + ((i - N / 2) & (n - 1))], dv), true};
+    if (j >= b && j < N - b) return Cv<R>{mk<R>(0, 0), false};
+    const int kx = (i < b) ? i : b + (N - 1 - i);
+    const int ky = (j < b) ? j : b + (N - 1 - j);
+    return Cv<R>{corner[ky * b2 + kx], true};
+  };
+  TwStage<R> tp;
+  tp.fetch(tw, n / 2);
+  // Fused CG step: its operands (x, p, s, the deapodisation factors and the
+  // boundary-column entries of z) are fetched together with the row, so that
+  // their loads overlap it; CPT entries per thread are held in registers, any
+  // further ones are read in place.  The stop flag is read by every thread: it
+  // changes only in the last CTA of this grid, after every CTA has read it.
+  constexpr int CPT = 4;
+  const bool fused = cg.x != nullptr;
+  bool run = false;
+  R a = (R)0;
+  double bd = 0.0;
+  C<R> xv[CPT], pv[CPT], sv[CPT], zb[CPT];
+  R dvv[CPT];
+  if (fused) {
+    run = cg.flag[0] == F_RUN;
+    a = (R)cg.alpha[0];
+    bd = cg.hs ? cg.beta[0] : 0.0;
+#pragma unroll
+    for (int u = 0; u < CPT; ++u) {
+      const int t = threadIdx.x + u * blockDim.x;
+      zb[u] = mk<R>(0, 0);
+      if (t < cnt) {
+        const int r = t / N, i = t - r * N, j = j0 + r;
+        const int64_t k = (int64_t)j0 * N + t;
+        dvv[u] = deap[i];
+        xv[u] = cg.x[k];
+        pv[u] = cg.p[k];
+        sv[u] = cg.s[k];
+        if (i < b || i >= N - b) {
+          if (j >= b && j < N - b) {
+            zb[u] = z[k];
+          } else {
+            const int kx = (i < b) ? i : b + (N - 1 - i);
+            const int ky = (j < b) ? j : b + (N - 1 - j);
+            zb[u] = corner[ky * b2 + kx];
+          }
+        }
+      }
+    }
+  }
   batched<PPT_ROW, C<R>>(
       nr * n,
       [&](int t) {
@@ -761,102 +849,121 @@ __global__ void k_adj2d_pass1(const C<R>* __restrict__ hbuf, const C<R>* __restr
         return side1[(int64_t)k * n + l];
       },
       [&](int t, C<R> v) { buf[t] = v; });
+  tp.store(tw, tws, n / 2);
   __syncthreads();
-  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, true);
-  batched<PPT_ROW, Cv<R>>(
-      nr * N,
-      [&](int t) {
-        const int r = t / N, i = t - r * N, j = j0 + r;
-        const R dv = deap[i];
-        if (dv != (R)0) return Cv<R>{cscale(buf[r * n + ((i - N / 2) & (n - 1))], dv), true};
-        if (j >= b && j < N - b) return Cv<R>{mk<R>(0, 0), false};  // x-side entries come from pass 2
-        const int kx = (i < b) ? i : b + (N - 1 - i);
-        const int ky = (j < b) ? j : b + (N - 1 - j);
-        return Cv<R>{corner[ky * b2 + kx], true};
-      },
-      [&](int t, Cv<R> o) {
-        if (o.ok) z[(int64_t)(j0 + t / N) * N + t % N] = o.v;
-      });
-  if (cg.x) {  // fused CG update of rows j0 .. j0+nr-1 (their x-side entries came from pass 2)
-    __shared__ int run;
-    __shared__ double wsum[32];
-    if (threadIdx.x == 0) run = (cg.flag[0] == 0);
-    __syncthreads();  // also orders this CTA's z stores before the reads below
-    if (!run) return;
-    const R a = (R)cg.alpha[0];
-    // direction of this step (CgStep::hs): p = s + beta p on the interior columns,
-    // with the beta of the previous step (beta = 0: p = s)
-    const bool dir = cg.hs != nullptr;
-    const double bd = dir ? cg.beta[0] : 0.0;
-    const bool b0 = bd == 0.0;
-    const R bt = (R)bd;
-    double acc = 0.0;
-    for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-      const int r = t / N, i = t - r * N;
-      const int64_t k = (int64_t)j0 * N + t;
-      C<R> xv = cg.x[k], pv = cg.p[k], sv = cg.s[k], zv = z[k];
-      if (dir && i >= b && i < N - b) {
-        pv = b0 ? sv : mk<R>(sv.x + bt * pv.x, sv.y + bt * pv.y);
-        cg.p[k] = pv;
-      }
-      xv.x += a * pv.x;
-      xv.y += a * pv.y;
-      sv.x -= a * zv.x;
-      sv.y -= a * zv.y;
-      cg.x[k] = xv;
-      cg.s[k] = sv;
-      acc += (double)sv.x * sv.x + (double)sv.y * sv.y;
-      if (dir) {  // the new s into this row's x-transform input (as k_fwd2d_pass1 lays it out)
-        const R dv = deap[i];
-        const int l = (i - N / 2) & (n - 1);
-        buf[r * n + l] = (dv != (R)0) ? cscale(sv, dv) : mk<R>(0, 0);
-        for (int q = N; q < n; q += N) buf[r * n + ((l + q) & (n - 1))] = mk<R>(0, 0);
+  fft_smem<R, PPT_ROW>(buf, nr, n, logn, tws, true);
+  if (!fused) {
+    batched<PPT_ROW, Cv<R>>(
+        cnt, [&](int t) { return zval(t, deap[t % N]); },
+        [&](int t, Cv<R> o) {
+          if (o.ok) z[(int64_t)j0 * N + t] = o.v;
+        });
+    return;
+  }
+  // z of the held entries (each thread reads only the transform positions of its
+  // own entries, which only it overwrites below)
+#pragma unroll
+  for (int u = 0; u < CPT; ++u) {
+    const int t = threadIdx.x + u * blockDim.x;
+    if (t < cnt) {
+      const Cv<R> o = zval(t, dvv[u]);
+      if (o.ok) {
+        z[(int64_t)j0 * N + t] = o.v;
+        zb[u] = o.v;
       }
     }
+  }
+  if (!run) {  // the solve has stopped: z only (the remaining entries too)
+    for (int t = threadIdx.x + CPT * blockDim.x; t < cnt; t += blockDim.x) {
+      const Cv<R> o = zval(t, deap[t % N]);
+      if (o.ok) z[(int64_t)j0 * N + t] = o.v;
+    }
+    return;
+  }
+  // direction of this step (CgStep::hs): p = s + beta p on the interior columns,
+  // with the beta of the previous step (beta = 0: p = s)
+  const bool dir = cg.hs != nullptr;
+  const bool b0 = bd == 0.0;
+  const R bt = (R)bd;
+  double acc = 0.0;
+  // x += alpha p, s -= alpha z, ||s||^2, and the new s into this row's x-transform
+  // input (as k_fwd2d_pass1 lays it out)
+  auto step = [&](int t, C<R> xo, C<R> po, C<R> so, C<R> zo, R dv) {
+    const int r = t / N, i = t - r * N;
+    const int64_t k = (int64_t)j0 * N + t;
+    if (dir && i >= b && i < N - b) {
+      po = b0 ? so : mk<R>(so.x + bt * po.x, so.y + bt * po.y);
+      cg.p[k] = po;
+    }
+    xo.x += a * po.x;
+    xo.y += a * po.y;
+    so.x -= a * zo.x;
+    so.y -= a * zo.y;
+    cg.x[k] = xo;
+    cg.s[k] = so;
+    acc += (double)so.x * so.x + (double)so.y * so.y;
     if (dir) {
-      __syncthreads();
-      fft_smem<R, PPT_ROW>(buf, nr, n, logn, tw, false);
-      for (int t = threadIdx.x; t < nr * n; t += blockDim.x) cg.hs[(int64_t)j0 * n + t] = buf[t];
+      const int l = (i - N / 2) & (n - 1);
+      buf[r * n + l] = (dv != (R)0) ? cscale(so, dv) : mk<R>(0, 0);
+      for (int q = N; q < n; q += N) buf[r * n + ((l + q) & (n - 1))] = mk<R>(0, 0);
     }
+  };
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  for (int u = 0; u < CPT; ++u) {
+    const int t = threadIdx.x + u * blockDim.x;
+    if (t < cnt) step(t, xv[u], pv[u], sv[u], zb[u], dvv[u]);
+  }
+  for (int t = threadIdx.x + CPT * blockDim.x; t < cnt; t += blockDim.x) {
+    const int64_t k = (int64_t)j0 * N + t;
+    const R dv = deap[t % N];
+    const Cv<R> o = zval(t, dv);
+    if (o.ok) z[k] = o.v;
+    step(t, cg.x[k], cg.p[k], cg.s[k], o.ok ? o.v : z[k], dv);
+  }
+  __shared__ double wsum[32];
+  __shared__ int last;
+  if (dir) {
     __syncthreads();
-    __shared__ int last;
-    if (threadIdx.x == 0) {
-      double tsum = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[w];
-      cg.part[blockIdx.x] = tsum;
-      last = 0;
-      if (cg.scal) {  // publish the partial, then count this CTA in
-        __threadfence();
-        last = (atomicAdd(cg.flag + FL_ARRIVE, 1) == (int)gridDim.x - 1);
-      }
-    }
-    __syncthreads();
-    if (!last) return;
-    // the last CTA: gamma' = sum of the partials in row order, beta, stop test
-    __threadfence();
-    double g = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) g += __ldcg(cg.part + i);
+    fft_smem<R, PPT_ROW>(buf, nr, n, logn, tws, false);
+    for (int t = threadIdx.x; t < nr * n; t += blockDim.x) cg.hs[(int64_t)j0 * n + t] = buf[t];
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = g;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double gs = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gs += wsum[w];
-      double* sc = cg.scal;
-      const double beta = gs / sc[S_GAMMA];
-      sc[S_BETA] = beta;
-      sc[S_GNEW] = gs;
-      sc[S_ITER] += 1.0;
-      if (!isfinite(beta)) cg.flag[0] = F_BREAK;
-      else if (gs <= sc[S_THR2]) cg.flag[0] = F_CONV;
-      else if (sc[S_ITER] >= sc[S_MAXIT]) cg.flag[0] = F_MAXIT;
-      cg.flag[FL_ARRIVE] = 0;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tsum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[w];
+    cg.part[blockIdx.x] = tsum;
+    last = 0;
+    if (cg.scal) {  // publish the partial, then count this CTA in
+      __threadfence();
+      last = (atomicAdd(cg.flag + FL_ARRIVE, 1) == (int)gridDim.x - 1);
     }
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last CTA: gamma' = sum of the partials in row order, beta, stop test
+  __threadfence();
+  double g = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) g += __ldcg(cg.part + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double gs = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) gs += wsum[w];
+    double* sc = cg.scal;
+    const double beta = gs / sc[S_GAMMA];
+    sc[S_BETA] = beta;
+    sc[S_GNEW] = gs;
+    sc[S_ITER] += 1.0;
+    if (!isfinite(beta)) cg.flag[0] = F_BREAK;
+    else if (gs <= sc[S_THR2]) cg.flag[0] = F_CONV;
+    else if (sc[S_ITER] >= sc[S_MAXIT]) cg.flag[0] = F_MAXIT;
+    cg.flag[FL_ARRIVE] = 0;
   }
 }
 
@@ -889,7 +996,7 @@ template <typename R>
 gs_status row_transform(Plan* P, PrecData<R>& D, const C<R>* v, C<R>* out, cudaStream_t st) {
   const int n = (int)P->n, logn = ilog2(P->n), N = (int)P->N;
   const int rows = 1;
-  size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+  size_t sh1 = ((size_t)rows * n + n / 2) * sizeof(C<R>);
   gs_status s = set_smem<R>((const void*)k_fwd2d_pass1<R>, sh1);
   if (s != GS_OK) return s;
   GS_LAUNCH(pname<R>("fwd2d_pass1<f32>", "fwd2d_pass1<f64>"), st,
@@ -929,7 +1036,7 @@ gs_status nfft_T(Plan* P, PrecData<R>& D, const C<R>* x, C<R>* y, const int32_t*
     // them from those of s and of the previous p in pass 2
     if (!pc) GS_TRY(row_transform<R>(P, D, x, D.hbuf, st));
     const int cols = pass_cols<R>();
-    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
+    size_t sh2 = ((size_t)cols * n + n / 2) * sizeof(C<R>);
     gs_status s = set_smem<R>((const void*)k_fwd2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("fwd2d_pass2<f32>", "fwd2d_pass2<f64>"), st,
@@ -1025,14 +1132,14 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
       GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
     }
     const int cols = pass_cols<R>();
-    size_t sh2 = (size_t)cols * n * sizeof(C<R>);
+    size_t sh2 = ((size_t)cols * n + n / 2) * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass2<R>, sh2);
     if (s != GS_OK) return s;
     GS_LAUNCH(pname<R>("adj2d_pass2<f32>", "adj2d_pass2<f64>"), st,
               k_adj2d_pass2<R><<<(n + b2 + cols - 1) / cols, fft_threads(cols, n), sh2, st>>>(D.grid, D.side, D.deap, N, n, logn, b,
                                                                               cols, D.tw, D.hbuf, z));
     const int rows = 1;
-    size_t sh1 = (size_t)rows * n * sizeof(C<R>);
+    size_t sh1 = ((size_t)rows * n + n / 2) * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
     if (b2 > 0 && !lat) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
