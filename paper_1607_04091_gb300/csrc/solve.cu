@@ -289,7 +289,14 @@ gs_status cg_iteration(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st)
   return GS_OK;
 }
 
-// Capture a whole CG pass as one graph: [enter kernel] -> while(cond) { iteration; cond kernel }.
+// CG iterations per execution of a captured while body.  An iteration that
+// starts after the stop flag is set changes nothing (every kernel of the step
+// tests the flag), so the body may hold several; the condition kernel, which
+// counts body executions and bounds the loop, and the re-evaluation of the
+// while node then come once per CG_UNROLL iterations.
+constexpr int CG_UNROLL = 2;
+
+// Capture a whole CG pass as one graph: [enter kernel] -> while(cond) { CG_UNROLL iterations; cond kernel }.
 template <typename R>
 gs_status build_cg_graph(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t st, cudaGraphExec_t* out) {
   cudaStream_t cs = P->cap_stream;
@@ -333,7 +340,8 @@ gs_status build_cg_graph(Plan* P, PrecData<R>& D, bool normal_eq, cudaStream_t s
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      gs_status s = cg_iteration<R>(P, D, normal_eq, cs);
+      gs_status s = GS_OK;
+      for (int u = 0; u < CG_UNROLL && s == GS_OK; ++u) s = cg_iteration<R>(P, D, normal_eq, cs);
       k_loop_cond<<<1, 1, 0, cs>>>(h, P->flag, P->scal);
       cudaGraph_t bb = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(cs, &bb);
@@ -654,7 +662,8 @@ gs_status add_solve_nodes(Plan* P, bool with_x0, cudaGraph_t G, cudaGraphNode_t 
   GS_TRY(add_while(outer_body, &n_ienter, hi, &n_inner, &inner_body));
   {
     GS_CUDA(cudaStreamBeginCaptureToGraph(cs, inner_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    gs_status sc = cg_iteration<float>(P, F, true, cs);
+    gs_status sc = GS_OK;
+    for (int u = 0; u < CG_UNROLL && sc == GS_OK; ++u) sc = cg_iteration<float>(P, F, true, cs);
     k_loop_cond<<<1, 1, 0, cs>>>(hi, P->flag, P->scal);
     cudaGraph_t bb = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &bb);
