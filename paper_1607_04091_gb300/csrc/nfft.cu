@@ -424,10 +424,9 @@ __global__ void k_reduce1d(const int32_t* __restrict__ work_start, const C<R>* _
 // boundary (or corner) channel sums over all work items: one CTA per channel,
 // threads stride over the work items, fixed-order tree sum
 template <typename R>
-__global__ void k_reduce_chan(const C<R>* __restrict__ part, int64_t stride, int64_t off, int nch,
-                              int nwork, C<R>* __restrict__ out) {
+__device__ __forceinline__ void reduce_chan_one(int c, const C<R>* __restrict__ part, int64_t stride, int64_t off,
+                                                int nwork, C<R>* __restrict__ out) {
   __shared__ C<R> red[256];
-  const int c = blockIdx.x;
   C<R> acc = mk<R>(0, 0);
   for (int wi = threadIdx.x; wi < nwork; wi += blockDim.x) acc = cadd(acc, part[wi * stride + off + c]);
   red[threadIdx.x] = acc;
@@ -437,6 +436,11 @@ __global__ void k_reduce_chan(const C<R>* __restrict__ part, int64_t stride, int
     __syncthreads();
   }
   if (threadIdx.x == 0) out[c] = red[0];
+}
+template <typename R>
+__global__ void k_reduce_chan(const C<R>* __restrict__ part, int64_t stride, int64_t off, int nch,
+                              int nwork, C<R>* __restrict__ out) {
+  reduce_chan_one<R>(blockIdx.x, part, stride, off, nwork, out);
 }
 
 // inverse FFT + crop + deapodise + boundary adjoint
@@ -625,12 +629,11 @@ __global__ void k_reduce2d_grid(const int32_t* __restrict__ work_start, const C<
 // neighbour bins are read once per CTA.  Bins and items are visited in the order
 // of k_reduce2d_grid, so the sums are identical.
 template <typename R>
-__global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restrict__ work_start,
-                                                         const C<R>* __restrict__ part, int64_t stride, int nbx,
-                                                         int m, int n, C<R>* __restrict__ grid) {
+__device__ __forceinline__ void reduce_grid16_tile(int bx, int by, const int32_t* __restrict__ work_start,
+                                                   const C<R>* __restrict__ part, int64_t stride, int nbx, int m,
+                                                   int n, C<R>* __restrict__ grid) {
   constexpr int T = 16;
   __shared__ int rng[9][2];  // [iy * 3 + ix] -> first, end item
-  const int bx = blockIdx.x, by = blockIdx.y;
   if (threadIdx.x < 9) {
     const int iy = threadIdx.x / 3, ix = threadIdx.x - 3 * iy;
     const int nb = ((by + iy - 1) & (nbx - 1)) * nbx + ((bx + ix - 1) & (nbx - 1));
@@ -676,6 +679,12 @@ __global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restri
   }
   grid[(int64_t)(bx * T + lx) * n + by * T + ly] = acc;
 }
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restrict__ work_start,
+                                                         const C<R>* __restrict__ part, int64_t stride, int nbx,
+                                                         int m, int n, C<R>* __restrict__ grid) {
+  reduce_grid16_tile<R>(blockIdx.x, blockIdx.y, work_start, part, stride, nbx, m, n, grid);
+}
 
 // side grids: which = 0 -> x-side k along y (segments S0; the work items of
 // the neighbouring bin rows are contiguous), which = 1 -> y-side k along x
@@ -683,12 +692,12 @@ __global__ void __launch_bounds__(256) k_reduce2d_grid16(const int32_t* __restri
 // list).  One CTA per (tile of output points, k, which); threads split the
 // contributing work items, fixed-order tree sum.
 template <typename R>
-__global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const int32_t* __restrict__ wcol,
-                                const int32_t* __restrict__ wcol_start, const C<R>* __restrict__ part,
-                                int64_t stride, int nbx, int tile, int m, int n, int b2, int which0,
-                                C<R>* __restrict__ side) {
+__device__ __forceinline__ void reduce_side_seg(int gb, int k, int which, const int32_t* __restrict__ work_start,
+                                                const int32_t* __restrict__ wcol,
+                                                const int32_t* __restrict__ wcol_start, const C<R>* __restrict__ part,
+                                                int64_t stride, int nbx, int tile, int m, int n, int b2,
+                                                C<R>* __restrict__ side) {
   __shared__ C<R> red[256];
-  const int which = which0 + (int)blockIdx.z, k = blockIdx.y, gb = blockIdx.x;
   const int pt = threadIdx.x % tile, wl = threadIdx.x / tile, nl = blockDim.x / tile;
   const int g = gb * tile + pt;
   const int PW = tile + 2 * m;
@@ -729,6 +738,41 @@ __global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const in
     for (int l = 0; l < nl; ++l) t = cadd(t, red[l * tile + pt]);
     side[((int64_t)which * b2 + k) * n + g] = t;
   }
+}
+template <typename R>
+__global__ void k_reduce2d_side(const int32_t* __restrict__ work_start, const int32_t* __restrict__ wcol,
+                                const int32_t* __restrict__ wcol_start, const C<R>* __restrict__ part,
+                                int64_t stride, int nbx, int tile, int m, int n, int b2, int which0,
+                                C<R>* __restrict__ side) {
+  reduce_side_seg<R>(blockIdx.x, blockIdx.y, which0 + (int)blockIdx.z, work_start, wcol, wcol_start, part, stride,
+                     nbx, tile, m, n, b2, side);
+}
+
+// All reductions of the 2D spread's partial tiles in one launch (16 x 16 tiles,
+// 256 threads): CTAs [0, nbx^2) sum grid tiles, the next 2 nbx b2 the x- and
+// y-side segments, the last b2^2 the corner channels.  Each CTA computes what the
+// separate kernels compute, in the same order; one launch on the adjoint's own
+// stream replaces three on two side branches.
+template <typename R>
+__global__ void __launch_bounds__(256) k_reduce2d_all(const int32_t* __restrict__ work_start,
+                                                      const int32_t* __restrict__ wcol,
+                                                      const int32_t* __restrict__ wcol_start,
+                                                      const C<R>* __restrict__ part, int64_t stride, int nbx, int m,
+                                                      int n, int b2, int nwork, int64_t coff, C<R>* __restrict__ grid,
+                                                      C<R>* __restrict__ side, C<R>* __restrict__ corner) {
+  const int ng = nbx * nbx, ns = nbx * b2;
+  int id = blockIdx.x;
+  if (id < ng) {
+    reduce_grid16_tile<R>(id % nbx, id / nbx, work_start, part, stride, nbx, m, n, grid);
+    return;
+  }
+  id -= ng;
+  if (id < 2 * ns) {
+    const int which = id / ns, r = id - which * ns;
+    reduce_side_seg<R>(r % nbx, r / nbx, which, work_start, wcol, wcol_start, part, stride, nbx, 16, m, n, b2, side);
+    return;
+  }
+  reduce_chan_one<R>(id - 2 * ns, part, stride, coff, nwork, corner);
 }
 
 // adjoint pass 2: inverse y-transform of grid columns -> hbuf[j][lx] (interior j),
@@ -1099,9 +1143,17 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
     const bool lat = P->lattice != 0;
     gs_status s = lat ? lattice_fold<R>(P, D, y, perm, st) : launch_spread2d<R>(P, D, y, perm, part, st);
     if (s != GS_OK) return s;
-    // the three reductions of the partials read the same input: side segments and
+    // 16 x 16 tiles with boundary columns: every reduction of the partials in one launch
+    const bool all1 = !lat && b2 > 0 && tile == 16 && P->nbx >= 3;
+    if (all1) {
+      const int nb = (int)(P->nbx * P->nbx + 2 * P->nbx * b2 + b2 * b2);
+      GS_LAUNCH(pname<R>("reduce2d_all<f32>", "reduce2d_all<f64>"), st,
+                k_reduce2d_all<R><<<nb, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, part, D.part_stride,
+                                                      P->nbx, m, n, b2, P->nwork, wsz, D.grid, D.side, D.corner));
+    }
+    // otherwise the three reductions read the same input: side segments and
     // corners on two side branches, the grid on st
-    if (b2 > 0 && !lat) {
+    if (b2 > 0 && !lat && !all1) {
       GS_TRY(fork_aux(P, st, 0));
       GS_TRY(fork_aux(P, st, 1));
       cudaStream_t a0 = side_stream(P, st, 0), a1 = side_stream(P, st, 1);
@@ -1118,7 +1170,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
                                                            D.corner));
     }
     dim3 rg(P->nbx, P->nby), rb(tile, tile);
-    if (lat) {
+    if (lat || all1) {
     } else if (tile == 16 && P->nbx >= 3)
       GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
                 k_reduce2d_grid16<R><<<rg, 256, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, m, n,
@@ -1127,7 +1179,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
       GS_LAUNCH(pname<R>("reduce2d_grid<f32>", "reduce2d_grid<f64>"), st,
                 k_reduce2d_grid<R><<<rg, rb, 0, st>>>(P->work_start, part, D.part_stride, P->nbx, tile, m, n,
                                                       D.grid));
-    if (b2 > 0 && !lat) {
+    if (b2 > 0 && !lat && !all1) {
       GS_CUDA(cudaGetLastError());
       GS_TRY(join_aux(P, st, 0));  // x-side grids: the last columns of pass 2
     }
@@ -1142,7 +1194,7 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
     size_t sh1 = ((size_t)rows * n + n / 2) * sizeof(C<R>);
     s = set_smem<R>((const void*)k_adj2d_pass1<R>, sh1);
     if (s != GS_OK) return s;
-    if (b2 > 0 && !lat) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
+    if (b2 > 0 && !lat && !all1) GS_TRY(join_aux(P, st, 1));  // corner sums: pass 1
     if (cg && cg->join_branch >= 0) GS_TRY(join_aux(P, st, cg->join_branch));
     const CgStep<R> cgv =
         cg ? *cg : CgStep<R>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, -1, nullptr, nullptr, nullptr};
