@@ -608,7 +608,7 @@ __device__ inline void win_elems(const float* taps, const int* pos, int rs0, int
 }
 }  // namespace tci
 
-static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
+static __global__ void __launch_bounds__(128, 7) k_interp2d_tc(
     const int32_t* __restrict__ work, const int32_t* __restrict__ order, const int32_t* __restrict__ fl,
     const float* __restrict__ win, const float2* __restrict__ w, const float2* __restrict__ bf,
     const float2* __restrict__ grid, const float2* __restrict__ hbuf, const float2* __restrict__ side, int n,
@@ -692,7 +692,7 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
       win_elems<2>(st + ST_WIN + W, pos, m0, lane, ks, th, tl);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        uint32_t ah[4], al[4], bh[2][3][2], bl[2][3][2];
+        uint32_t ah[4], al[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {  // fragment element q = row half + 2 column half
           const int i = 2 * (q & 1) + (q >> 1);
@@ -700,17 +700,17 @@ static __global__ void __launch_bounds__(128, 6) k_interp2d_tc(
           al[q] = (ks[i] == k) ? tl[i] : 0u;
         }
 #pragma unroll
-        for (int nbk = 0; nbk < 3; ++nbk) {
-          tc::load_bT(sm + I_GR, LDQ, 8 * nbk, 8 * k, lane, bh[0][nbk], bl[0][nbk]);
-          tc::load_bT(sm + I_GI, LDQ, 8 * nbk, 8 * k, lane, bh[1][nbk], bl[1][nbk]);
-        }
-#pragma unroll
-        for (int term = 0; term < 3; ++term)
+        for (int ri = 0; ri < 2; ++ri) {  // real, then imaginary part of G: 12 fragment registers live
+          uint32_t bh[3][2], bl[3][2];
 #pragma unroll
           for (int nbk = 0; nbk < 3; ++nbk)
+            tc::load_bT(sm + (ri ? I_GI : I_GR), LDQ, 8 * nbk, 8 * k, lane, bh[nbk], bl[nbk]);
 #pragma unroll
-            for (int ri = 0; ri < 2; ++ri)
-              mma(acc[3 * ri + nbk], term == 2 ? al : ah, term == 1 ? bl[ri][nbk] : bh[ri][nbk]);
+          for (int term = 0; term < 3; ++term)
+#pragma unroll
+            for (int nbk = 0; nbk < 3; ++nbk)
+              mma(acc[3 * ri + nbk], term == 2 ? al : ah, term == 1 ? bl[nbk] : bh[nbk]);
+        }
       }
       // interior term: the lane holds H[s][x] for its two samples and six columns x;
       // sum wx_s[x - px_s] H[s][x] over them, then over the quad's four lanes
