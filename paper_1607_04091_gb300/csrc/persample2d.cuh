@@ -618,6 +618,9 @@ static __global__ void __launch_bounds__(128, 7) k_interp2d_tc(
   extern __shared__ __align__(16) float sm[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
+  // a kernel launched as this one's programmatic dependent (the spread of a CG
+  // step) may start its set-up now; it waits for this grid before reading y
+  asm volatile("griddepcontrol.launch_dependents;");
   const int it = order[blockIdx.x];  // work item (larger items launch first)
   const int bin = work[3 * it], s0 = work[3 * it + 1], s1 = work[3 * it + 2];
   const int ox = (bin % nbx) * TILE, oy = (bin / nbx) * TILE;
@@ -918,11 +921,22 @@ gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t*
     const size_t sh = (size_t)tc5::N_SMEM * sizeof(float);
     gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc5, sh);
     if (e != GS_OK) return e;
+    // a programmatic dependent launch: the CTAs' set-up (TMEM, barriers, operand
+    // buffers, table staging) overlaps the end of the kernel before it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)P->nwork);
+    cfg.blockDim = dim3(tc5::THREADS);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     GS_LAUNCH("spread2d<f32>", st,
-              k_spread2d_tc5<<<P->nwork, tc5::THREADS, sh, st>>>(P->work, P->work_order, P->fl, (const float*)D.win,
-                                                        (const float2*)D.w, (const float2*)D.bf, (const float2*)u, perm,
-                                                        P->M, P->nbx, (float2*)part, D.part_stride,
-                                                        P->flag + FL_TIMEOUT));
+              GS_CUDA(cudaLaunchKernelEx(&cfg, k_spread2d_tc5, P->work, P->work_order, P->fl, (const float*)D.win,
+                                         (const float2*)D.w, (const float2*)D.bf, (const float2*)u, perm, P->M,
+                                         P->nbx, (float2*)part, D.part_stride, P->flag + FL_TIMEOUT)));
     GS_CUDA(cudaGetLastError());
     return GS_OK;
   }

@@ -169,7 +169,7 @@ constexpr int PART_U = 6;
 __device__ __forceinline__ void stage(float* sg, int tid, int sb, int nb, const float* __restrict__ win,
                                       const float2* __restrict__ w, const float2* __restrict__ bf,
                                       const float2* __restrict__ u, int ui,
-                                      const int32_t* __restrict__ fl, int64_t M) {
+                                      const int32_t* __restrict__ fl, int64_t M, bool with_u = true) {
   const int j = tid & (SB - 1), part = tid >> 4;
   if (j >= nb) return;
   const int64_t s = sb + j;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void stage(float* sg, int tid, int sb, int nb, const 
     case 6:
       cp8(sg + S_W + 4 * j, w + s);
       cp8(sg + S_W + 4 * j + 2, w + M + s);
-      cp8(sg + S_U + 2 * j, u + ui);
+      if (with_u) cp8(sg + S_U + 2 * j, u + ui);
       break;
     default:
       cp4(sg + S_FL + 2 * j, fl + s);
@@ -247,10 +247,12 @@ static __global__ void __launch_bounds__(160, 4) k_spread2d_tc5(
   };
   // batches 0 .. STAGES-2 in flight before the loop (one copy group each)
 #pragma unroll
+  // (the sample values u may be written by the kernel before this one in the
+  // stream: they are read only after griddepcontrol.wait below)
   for (int pb = 0; pb < STAGES - 1; ++pb) {
     if (pb < nbat && tid < BUILDERS)
       stage(sm + O_STAGE + pb * S_SIZE, tid, s0 + pb * SB, min(SB, s1 - s0 - pb * SB), win, w, bf, u, uindex(pb),
-            fl, M);
+            fl, M, false);
     cp_commit();
   }
   int ui_next = (tid < BUILDERS) ? uindex(STAGES - 1) : 0;  // loaded one batch before it is staged
@@ -267,6 +269,19 @@ static __global__ void __launch_bounds__(160, 4) k_spread2d_tc5(
 #pragma unroll
     for (int i = 0; i < NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + i)));
     *abort_s = 0;
+  }
+  // Launched as a programmatic dependent of the interpolation in a CG step, the
+  // CTA reaches this point while that kernel may still run: everything above
+  // reads only the plan's tables.  Wait for the previous kernel's writes, then
+  // stage the sample values of the first batches.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (tid < BUILDERS && (tid >> 4) == PART_U) {
+#pragma unroll
+    for (int pb = 0; pb < STAGES - 1; ++pb) {
+      const int64_t s = s0 + (int64_t)pb * SB + (tid & (SB - 1));
+      if (pb < nbat && s < s1)
+        *reinterpret_cast<float2*>(sm + O_STAGE + pb * S_SIZE + S_U + 2 * (tid & (SB - 1))) = u[uindex(pb)];
+    }
   }
   fence_before();
   __syncthreads();
