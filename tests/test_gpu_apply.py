@@ -218,3 +218,32 @@ def test_2d_tensor_core_and_scalar_paths(monkeypatch):
     # the two float32 evaluations differ only by rounding
     assert rel(out[False][0], out[True][0]) < tol
     assert rel(out[False][1], out[True][1]) < tol
+
+
+@pytest.mark.parametrize("prec", [gs.GS_FP32, gs.GS_FP64])
+def test_adjoint_right_after_forward_on_one_stream(prec):
+    """T^H (T x) with both applies queued back to back on one stream equals, bit for
+    bit, the same two applies with the stream synchronised and q copied in between.
+    The float32 adjoint's first kernel is launched as a programmatic dependent of
+    the kernel before it (the forward interpolation here) and reads q only after
+    waiting for that grid; an early read would show here."""
+    g = synth.rng(77)
+    xi2 = g.uniform(-48, 48, size=(6001, 2))
+    plan = gs.Plan.plan_2d(xi2, 4, 5, direct=0)
+    x = dev(rand_c(g, plan.ncoef), prec)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        zs = []
+        for _ in range(3):
+            q = plan.T(x, prec)
+            zs.append(plan.TH(q, prec))
+    st.synchronize()
+    q = plan.T(x, prec)
+    torch.cuda.synchronize()
+    q2 = q.clone()
+    torch.cuda.synchronize()
+    z = plan.TH(q2, prec)
+    torch.cuda.synchronize()
+    ref = z.cpu().numpy()
+    for zq in zs:
+        assert np.array_equal(zq.cpu().numpy(), ref)
