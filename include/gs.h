@@ -189,6 +189,10 @@ gs_status gs_solve(gs_plan plan, const void* y, void* x, const gs_solve_opts* op
  * previous solve times a per-iteration time model), and the call waits once, when
  * all have finished.  Other options run gs_solve per problem on those streams as
  * they come free.  y[i], x[i] as in gs_solve; infos (host, B entries) may be NULL.
+ * A plan's first batch call synchronises the device once and rebuilds its cached
+ * graphs: in a batch, and in every later call on that plan, the 2D spread and
+ * reductions launch without overlapping the kernel before them (early-launched
+ * CTAs would hold SM space the other problems' kernels can use).
  * Returns the first non-OK status of any problem (GS_ENOTCONV included). */
 gs_status gs_solve_batch(const gs_plan* plans, int B, const void* const* y, void* const* x,
                          const gs_solve_opts* opts, gs_solve_info* infos, void* stream);

@@ -155,6 +155,10 @@ struct Plan {
   bool solve_kernels_warm = false;  // the solve's kernels ran once outside any capture
   uint64_t uid = 0;                 // unique per plan in the process (batch-graph cache key)
   int last_iters = 0;               // CG iterations of the last graph solve (batch schedule cost)
+  // the 2D spread and the partial-tile reductions launch as programmatic dependents
+  // of the kernel before them, so that their CTAs' set-up overlaps its end; off for
+  // a plan once it is solved in a batch (see solve_batch)
+  bool pdl = true;
 };
 
 // Work launched on side_stream(P, st, i) between fork_aux(P, st, i) and

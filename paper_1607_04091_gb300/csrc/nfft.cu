@@ -762,6 +762,7 @@ __global__ void __launch_bounds__(256) k_reduce2d_all(const int32_t* __restrict_
                                                       C<R>* __restrict__ side, C<R>* __restrict__ corner) {
   const int ng = nbx * nbx, ns = nbx * b2;
   int id = blockIdx.x;
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the partial tiles of the spread before it
   if (id < ng) {
     reduce_grid16_tile<R>(id % nbx, id / nbx, work_start, part, stride, nbx, m, n, grid);
     return;
@@ -1147,9 +1148,19 @@ static gs_status nfft_TH_part(Plan* P, PrecData<R>& D, const C<R>* y, C<R>* z, c
     const bool all1 = !lat && b2 > 0 && tile == 16 && P->nbx >= 3;
     if (all1) {
       const int nb = (int)(P->nbx * P->nbx + 2 * P->nbx * b2 + b2 * b2);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)nb);
+      cfg.blockDim = dim3(256);
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = P->pdl ? 1 : 0;  // a programmatic dependent of the spread
       GS_LAUNCH(pname<R>("reduce2d_all<f32>", "reduce2d_all<f64>"), st,
-                k_reduce2d_all<R><<<nb, 256, 0, st>>>(P->work_start, P->wcol, P->wcol_start, part, D.part_stride,
-                                                      P->nbx, m, n, b2, P->nwork, wsz, D.grid, D.side, D.corner));
+                GS_CUDA(cudaLaunchKernelEx(&cfg, k_reduce2d_all<R>, P->work_start, P->wcol, P->wcol_start,
+                                           (const C<R>*)part, D.part_stride, (int)P->nbx, m, n, b2, (int)P->nwork,
+                                           (int64_t)wsz, D.grid, D.side, D.corner)));
     }
     // otherwise the three reductions read the same input: side segments and
     // corners on two side branches, the grid on st

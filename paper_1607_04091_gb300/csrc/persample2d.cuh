@@ -921,8 +921,8 @@ gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t*
     const size_t sh = (size_t)tc5::N_SMEM * sizeof(float);
     gs_status e = set_smem_attr<R>((const void*)k_spread2d_tc5, sh);
     if (e != GS_OK) return e;
-    // a programmatic dependent launch: the CTAs' set-up (TMEM, barriers, operand
-    // buffers, table staging) overlaps the end of the kernel before it
+    // a programmatic dependent launch (unless P->pdl is off): the CTAs' set-up (TMEM,
+    // barriers, operand buffers, table staging) overlaps the end of the kernel before it
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)P->nwork);
     cfg.blockDim = dim3(tc5::THREADS);
@@ -932,7 +932,7 @@ gs_status launch_spread2d(Plan* P, PrecData<R>& D, const C<R>* u, const int32_t*
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = P->pdl ? 1 : 0;
     GS_LAUNCH("spread2d<f32>", st,
               GS_CUDA(cudaLaunchKernelEx(&cfg, k_spread2d_tc5, P->work, P->work_order, P->fl, (const float*)D.win,
                                          (const float2*)D.w, (const float2*)D.bf, (const float2*)u, perm, P->M,

@@ -980,8 +980,37 @@ gs_status solve_batch_graphs(Plan** plans, int B, const double* const* y, double
   return first;
 }
 
+// In a batch the problems' kernels run side by side, and CTAs launched early to
+// wait for the kernel before them (the programmatic launches of the spread and the
+// reductions) would only hold SM space that other problems' kernels could use:
+// measured on the 512-problem bench batch, 39.4 problems/s with them against 41.2
+// without.  So a plan solved in a batch launches without them from then on; its
+// graphs, captured with them, are rebuilt once (after a device synchronisation,
+// so that no launch of a destroyed graph is in flight).
+static gs_status batch_launch_mode(Plan** plans, int B) {
+  bool stale = false;
+  for (int p = 0; p < B; ++p) stale = stale || plans[p]->pdl;
+  if (!stale) return GS_OK;
+  GS_CUDA(cudaDeviceSynchronize());
+  for (int p = 0; p < B; ++p) {
+    Plan* P = plans[p];
+    if (!P->pdl) continue;
+    P->pdl = false;
+    for (int i = 0; i < 2; ++i) {
+      if (P->solve_exec[i]) cudaGraphExecDestroy(P->solve_exec[i]);
+      P->solve_exec[i] = nullptr;
+      if (P->f.cg_exec[i]) cudaGraphExecDestroy(P->f.cg_exec[i]);
+      P->f.cg_exec[i] = nullptr;
+      if (P->d.cg_exec[i]) cudaGraphExecDestroy(P->d.cg_exec[i]);
+      P->d.cg_exec[i] = nullptr;
+    }
+  }
+  return GS_OK;
+}
+
 gs_status solve_batch(Plan** plans, int B, const double* const* y, double* const* x, const gs_solve_opts& o,
                       gs_solve_info* infos, cudaStream_t st) {
+  GS_TRY(batch_launch_mode(plans, B));
   bool all_graph = true;
   for (int p = 0; p < B; ++p) all_graph = all_graph && graph_solve_ok(plans[p], o);
   if (all_graph) return solve_batch_graphs(plans, B, y, x, o, infos, st);

@@ -481,6 +481,9 @@ static __global__ void __launch_bounds__(160, 4) k_spread2d_tc5(
     }
     out[o] = make_float2(re, im);
   }
+  // the reductions launched as this kernel's programmatic dependent may start
+  // once every CTA has written its partial tile (they wait for the grid anyway)
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 
 }  // namespace dev
