@@ -148,3 +148,24 @@ def test_batch_from_learned_starts():
     for y, x, info in zip(yn, xs, infos):
         assert info["status"] == gs.GS_OK, info
         assert rel_normres(op, y, x.cpu().numpy()) <= 1.1e-6
+
+
+def test_batch_after_single_solves_matches_them():
+    """Plans solved one at a time first (their graphs captured with the spread and
+    the partial-tile reductions launched as programmatic dependents), then all in
+    one batch call, which rebuilds those graphs without the programmatic launches:
+    the batch returns the same x as the single solves, bit for bit (the launch mode
+    changes when kernels start, not what they compute)."""
+    probs = small_batch(6)
+    plans, ys = [], []
+    g = synth.rng(12)
+    for pr in probs:
+        y0 = oracle_op(pr).apply(pr.x_true)
+        ys.append(torch.tensor(y0 + 1e-3 * synth.complex_gaussian(y0.size, g), device="cuda"))
+        plans.append(make_plan(pr))
+    singles = [p.solve(y, tol=1e-6, maxit=4000)[0] for p, y in zip(plans, ys)]
+    xs = [torch.zeros(p.ncoef, dtype=torch.complex128, device="cuda") for p in plans]
+    infos = gs.gs_solve_batch([p.handle for p in plans], ys, xs, tol=1e-6, maxit=4000)
+    for k, info in enumerate(infos):
+        assert info["status"] == gs.GS_OK, (k, info)
+        assert torch.equal(xs[k], singles[k]), k
