@@ -380,7 +380,7 @@ def main():
     shares = {k: round(v[1] / prof_total, 4) for k, v in ranked[:12]}
     apply = apply_timings(gs, plan, flush, M, 2**J, b, peak)
 
-    # ---- plain float64 CGLS on the same problem (the spec comparison)
+    # ---- plain float64 CGLS on the same problem (what the mixed solve is measured against)
     fp64 = None
     if args.fp64_steps > 0:
         fe = []
@@ -555,7 +555,7 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
             res[key].append((info["iterations"], a.elapsed_time(b), info["rel_normres"]))
     summ = {k: {"iterations": float(np.mean([r[0] for r in v])), "ms": float(np.mean([r[1] for r in v])),
                 "max_rel_normres": float(max(r[2] for r in v))} for k, v in res.items()}
-    # the spec comparison on the same held-out problems: learned start +
+    # the headline comparison on the same held-out problems: learned start +
     # batched (one graph, one plan per problem) + mixed precision, against plain
     # float64 CGLS from zero one problem at a time
     tests = [problem(100000 + k) for k in range(ntest)]
@@ -588,7 +588,7 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
                      "from zero on the first fp64_problems of them"}
     return {"train_pairs": ntrain, "test_problems": ntest, "epochs": epochs, "batch": batch,
             "loss_first": losses[0], "loss_last": float(np.mean(losses[-max(1, ntrain // batch):])),
-            "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ, "north_star": north,
+            "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ, "vs_fp64_cgls": north,
             "net": "6 conv3x3 layers 2-32-32-32-32-32-2, ReLU, residual, bf16 inference weights"}
 
 

@@ -59,7 +59,7 @@ typedef enum {
   GS_ENOTCONV = 4,      /* gs_solve hit maxit before the tolerance */
   GS_EBREAKDOWN = 5,    /* CGLS breakdown: ||T p|| = 0 or a non-finite step */
   GS_ETIMEOUT = 6,      /* a bounded device wait gave up */
-  GS_EUNSUPPORTED = 7   /* a valid request this build does not implement */
+  GS_EUNSUPPORTED = 7   /* a valid request the library does not implement */
 } gs_status;
 
 /* Arithmetic of one apply. */
