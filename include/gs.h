@@ -249,8 +249,8 @@ gs_status gs_cnn_pair(gs_plan plan, const void* y, const void* x, float* u_img, 
 
 /* Least squares from the learned warm start: u = T^H y (float32), x0 = rms(u) *
  * net(u / rms(u)) (bfloat16 weights), then gs_solve from x0 -- or from zero when
- * ||T^H (y - T x0)|| >= ||T^H y||, the plain method being the fallback and the
- * judge.  2D plans whose N x N grid is the network's image.  *used_warm_start
+ * ||T^H (y - T x0)|| >= ||T^H y||: the plain method is the fallback, and its
+ * residual decides.  2D plans whose N x N grid is the network's image.  *used_warm_start
  * (may be NULL) tells which start was taken.  Other arguments as gs_solve. */
 gs_status gs_solve_learned(gs_plan plan, gs_cnn net, const void* y, void* x, const gs_solve_opts* opts,
                            gs_solve_info* info, int* used_warm_start, void* stream);

@@ -58,7 +58,7 @@ def test_cfg2_1d_db4_J10_full_oracle(prec):
     assert rel(plan.T(dev(xstar, prec), prec).cpu().numpy(), y_ref) < tol
     u = g.standard_normal(xi.size) + 1j * g.standard_normal(xi.size)
     assert rel(plan.TH(dev(u, prec), prec).cpu().numpy(), op.adjoint(u)) < tol
-    if prec == gs.GS_FP32:  # the mixed solve to 1e-6, judged by the oracle's float64 residual
+    if prec == gs.GS_FP32:  # the mixed solve to 1e-6, checked by the oracle's float64 residual
         y = y_ref + 1e-3 * synth.complex_gaussian(xi.size, g) * np.sqrt(mu)
         x, info = plan.solve(torch.tensor(y, device="cuda"), tol=1e-6)
         assert info["status"] == gs.GS_OK
