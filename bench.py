@@ -581,14 +581,14 @@ def learned_bench(plan, xi, mu, ntrain, ntest, dev, epochs=12, batch=8, lr=1e-3)
         torch.cuda.synchronize()
         t64.append(a.elapsed_time(b))
     del bplans
-    north = {"learned_batched_mixed_ms_per_problem": t_lbm, "fp64_cgls_ms_per_problem": float(np.mean(t64)),
+    versus = {"learned_batched_mixed_ms_per_problem": t_lbm, "fp64_cgls_ms_per_problem": float(np.mean(t64)),
              "speedup": float(np.mean(t64)) / t_lbm, "problems": ntest, "fp64_problems": nf,
              "converged": sum(1 for i in binf if i["status"] == gs.GS_OK and i["rel_normres"] <= TOL),
              "note": "gs_solve_batch_learned on the held-out problems (one graph) vs gs_solve float64 CGLS "
                      "from zero on the first fp64_problems of them"}
     return {"train_pairs": ntrain, "test_problems": ntest, "epochs": epochs, "batch": batch,
             "loss_first": losses[0], "loss_last": float(np.mean(losses[-max(1, ntrain // batch):])),
-            "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ, "vs_fp64_cgls": north,
+            "data_s": t_data, "train_s": t_train, "warm_start_used": used, **summ, "vs_fp64_cgls": versus,
             "net": "6 conv3x3 layers 2-32-32-32-32-32-2, ReLU, residual, bf16 inference weights"}
 
 
