@@ -306,6 +306,32 @@ def test_cgls_recovers_and_matches_qr(p, J, M):
     assert np.max(np.abs(x1 - x2)) / np.max(np.abs(x2)) < 1e-10
 
 
+def test_cgls_iterates_minimise_over_the_krylov_space():
+    """The k-th CGLS iterate from x = 0 is the minimiser of ||y - A x|| over the
+    Krylov space span{A^H y, (A^H A) A^H y, ..., (A^H A)^(k-1) A^H y} (Sec. 2: CGLS is
+    CG on the normal equations).  Computed here directly: an orthonormal basis of
+    that space by QR, then least squares in it.  Pins every iterate of the oracle's
+    recurrences, not only their limit (a wrong beta or alpha still converges, more
+    slowly, but leaves the Krylov minimisers)."""
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((40, 12)) + 1j * rng.standard_normal((40, 12))
+    y = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    AH = A.conj().T
+    b = AH @ y
+    for k in range(1, 8):
+        xk, it, _ = cgls(lambda v: A @ v, lambda v: AH @ v, y, tol=0.0, maxit=k)
+        assert it == k
+        K = np.empty((12, k), dtype=complex)
+        v = b.copy()
+        for j in range(k):
+            K[:, j] = v
+            v = AH @ (A @ v)
+        Q, _ = np.linalg.qr(K)
+        z = np.linalg.lstsq(A @ Q, y, rcond=None)[0]
+        xs = Q @ z
+        assert np.max(np.abs(xk - xs)) / np.max(np.abs(xs)) < 1e-10, k
+
+
 @pytest.mark.parametrize("name", ["radial_db4_J8", "grid_db4_J9"])
 def test_golden_files_match_their_cases(name):
     # the stored sampled rows are the oracle's T x of the case's seeded inputs
